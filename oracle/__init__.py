@@ -82,6 +82,10 @@ def _load():
             L.oracle_solve.argtypes = [p, ctypes.c_int, p, i32, ctypes.c_int, i64, dbl, dbl, u64, p, p,
                                        ctypes.POINTER(_Result)]
             L.oracle_solve.restype = ctypes.c_int
+            L.oracle_source_coin.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+            L.oracle_source_coin.restype = ctypes.c_int
+            L.oracle_select_in_edge.argtypes = [p, ctypes.c_int32, ctypes.c_uint32]
+            L.oracle_select_in_edge.restype = i64
             L.oracle_bruteforce_spread.argtypes = [p, p, i32, p, p, p]
             L.oracle_bruteforce_spread.restype = dbl
             _lib = L
@@ -124,6 +128,10 @@ class Graph:
             _lib.oracle_graph_free(h)
             self._h = None
 
+    def select_in_edge(self, v: int, r: int) -> int:
+        """CSR id of v's live in-edge for the draw r, or -1."""
+        return int(_load().oracle_select_in_edge(self._h, v, r))
+
     def arrays(self):
         """(row_ptr int64[n+1], src int32[m], dst int32[m], thr uint32[m], input_index int64[m])"""
         rp = np.empty(self.n + 1, np.int64)
@@ -133,6 +141,11 @@ class Graph:
         ii = np.empty(self.m, np.int64)
         _load().oracle_graph_export(self._h, _ptr(rp), _ptr(s), _ptr(d), _ptr(t), _ptr(ii))
         return rp, s, d, t, ii
+
+
+def source_coin(x1: int, p32: int) -> bool:
+    """Source coin rule: x1 < p32, with p32 = 0xFFFFFFFF certain."""
+    return bool(_load().oracle_source_coin(x1, p32))
 
 
 class Query:

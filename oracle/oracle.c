@@ -178,12 +178,25 @@ typedef struct {
   uint64_t seed;
 } oracle_ctx;
 
+/* Source coin with probability p32 / 2^32: x1 < p32, and p32 = 0xFFFFFFFF is certain. */
+int oracle_source_coin(uint32_t x1, uint32_t p32) {
+  if (p32 == 0xFFFFFFFFu) return 1;
+  return x1 < p32;
+}
+
 static int coin_says_source(const oracle_ctx* c, int32_t u, uint32_t x1) {
   if (!c->is_suspect[u]) return 0;
   if (!c->p32) return 1;
-  uint32_t p = c->p32[u];
-  if (p == 0xFFFFFFFFu) return 1;
-  return x1 < p;
+  return oracle_source_coin(x1, c->p32[u]);
+}
+
+/* Live in-edge of v for the draw r (Sec. 2.1 live-edge model): the first in-edge j with
+ * r < thr[j], i.e. in-edge j is chosen for r in [thr[j-1], thr[j]); -1 when r is at or
+ * above the node's in-sum (no live in-edge). */
+int64_t oracle_select_in_edge(const oracle_graph* g, int32_t v, uint32_t r) {
+  for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j)
+    if (r < g->thr[j]) return j;
+  return -1;
 }
 
 /* Outcome codes of one attempt. */
@@ -224,11 +237,7 @@ int oracle_attempt(const oracle_ctx* c, uint64_t a, int32_t* nodes, int32_t* edg
     draw_node(c->seed, a, v, x);
     if (coin_says_source(c, v, x[1])) return ORACLE_HIT;
     if (s > g->n) return ORACLE_STEP_CAP;
-    uint32_t r = x[0];
-    int64_t chosen = -1;
-    for (int64_t j = g->row_ptr[v]; j < g->row_ptr[v + 1]; ++j) {
-      if (r < g->thr[j]) { chosen = j; break; }
-    }
+    int64_t chosen = oracle_select_in_edge(g, v, x[0]);
     if (chosen < 0) return ORACLE_MISS_NO_EDGE;
     int32_t u = g->src[chosen];
     if (c->edge_removed && c->edge_removed[chosen]) return ORACLE_MISS_REMOVED;

@@ -65,6 +65,47 @@ def test_graph_build_rejects_overweight_and_range():
         oracle.Graph(2, src, dst, np.array([1, 1], np.uint32))
 
 
+def test_select_in_edge_boundaries():
+    """Inverse-CDF selection: in-edge j is live exactly for r in [thr[j-1], thr[j]), so the
+    number of draws choosing it is w_fixed[j] (probability w / 2^32, Sec. 2.1)."""
+    w = np.array([5, 0, 7, 0xFFFFFFF0 - 12], np.uint32)   # sum 0xFFFFFFF0 < 2^32 - 1
+    g = oracle.Graph(2, np.array([1, 0, 1, 0], np.int32), np.array([0, 0, 0, 0], np.int32), w)
+    assert [g.select_in_edge(0, r) for r in (0, 4)] == [0, 0]
+    assert g.select_in_edge(0, 5) == 2            # the zero-weight edge 1 is never live
+    assert g.select_in_edge(0, 11) == 2 and g.select_in_edge(0, 12) == 3
+    assert g.select_in_edge(0, 0xFFFFFFEF) == 3
+    assert g.select_in_edge(0, 0xFFFFFFF0) == -1 and g.select_in_edge(0, 0xFFFFFFFF) == -1
+    assert g.select_in_edge(1, 0) == -1           # no in-edges
+
+
+def test_source_coin_boundaries():
+    """Source coin: probability p32 / 2^32 (x1 < p32), p32 = 0xFFFFFFFF certain."""
+    assert not oracle.source_coin(0, 0) and not oracle.source_coin(0xFFFFFFFF, 0)
+    assert oracle.source_coin(9, 10) and not oracle.source_coin(10, 10)
+    assert oracle.source_coin(0xFFFFFFFF, 0xFFFFFFFF) and oracle.source_coin(0, 0xFFFFFFFF)
+    assert not oracle.source_coin(0xFFFFFFFE, 0xFFFFFFFE)
+
+
+def test_attempt_walks_are_self_avoiding_chains():
+    """Every attempt, hit or miss, walks a self-avoiding chain of live in-edges (the
+    backward chain of one live-edge world, Sec. 3.1 "Self-avoiding")."""
+    for gseed in range(6):
+        n, src, dst, w = random_tiny(500 + gseed, n=6, m=14)
+        g = oracle.Graph(n, src, dst, w)
+        rp, s, d, thr, ii = g.arrays()
+        q = oracle.Query(g, np.array([gseed % n], np.int32), seed=gseed)
+        outs = set()
+        for a in range(3000):
+            r, nodes, edges = q.attempt(a)
+            outs.add(r)
+            assert len(set(nodes.tolist())) == len(nodes)
+            for i, e in enumerate(edges):
+                assert d[e] == nodes[i] and s[e] == nodes[i + 1]
+            if r == oracle.MISS_CYCLE:  # the last choice closed a cycle
+                pass
+        assert oracle.STEP_CAP not in outs
+
+
 # ----------------------------------------------------------------------------- brute force closed forms
 def test_bruteforce_closed_forms():
     """Live-edge model closed forms (Sec. 2.1): edge, chain, cycle, independent suspects, removal."""
@@ -326,6 +367,14 @@ def test_check_behaviour():
     assert ok
     ok, et = oracle.check(2 * 0.6 * 2851 * 1024, 0.6 * 2851 * 1024, 2851 * 1024, 11, 0.1, lam1)
     assert not ok and et > 0.1
+    # with unbiased in-sample coverage the bound vanishes as the samples double without
+    # end (eps_2, eps_3 are Chernoff deviations of |R'_t| = Lambda 2^(t-1) samples)
+    size = 2851 * 2 ** 39
+    ok, et = oracle.check(0.6 * size, 0.6 * size, size, 40, 0.1, lam1)
+    assert ok and et < 1e-3
+    # the bound never drops below the in-sample bias term eps_1 (1 - 1/e - eps)
+    ok, et = oracle.check(1.2 * 0.6 * size, 0.6 * size, size, 40, 0.1, lam1)
+    assert et >= 0.2 * (1 - 1 / math.e - 0.1)
 
 
 # ----------------------------------------------------------------------------- end-to-end quality
