@@ -1,0 +1,290 @@
+"""Benchmark: HSAWs/s of the eSI billion-edge solve on one GB300 (or N independent replicas).
+
+Workload (default): R-MAT scale 26 (67,108,864 nodes, 1,073,741,824 edges, a,b,c =
+0.57, 0.19, 0.19), weighted-cascade LT weights in uint32 fixed point, |S| = 1,000 random
+sources, k = 1,000, the sample-doubling stopping rule with eps = 0.1, delta = 1/n.  A step
+is one full solve (sampling, ordered compaction, counting, inverted index, greedy,
+out-of-sample coverage, Check) on the resident graph; value = HSAWs used by the solves
+(|R_t| + |R'_t|) / device time.  The graph (9.6 GB on the device) is larger than L2, so
+no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hsaw|reference]
+
+Under torchrun with N ranks each rank solves its own replica (its own walk seed);
+value = HSAWs of all ranks / the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "HSAWs/s at 1B edges (eSI stop-rule solve, R-MAT scale 26)"
+UNIT = "HSAW/s"
+BYTES_PER_STEP = 96  # three random 32-byte sectors per live-edge draw: node record, threshold, tail node
+# DRAM bytes per attempt of the sampler kernel from an ncu capture, keyed by the hash of
+# the sampler source it was taken on (the figure is void once the kernel changes).
+NCU_TRAFFIC = {}
+
+
+def sampler_hash():
+    h = hashlib.sha1()
+    for f in ("sample.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1702_05854_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def make_workload(scale):
+    t0 = time.time()
+    d = synth.workload_c3(scale)
+    d["gen_s"] = time.time() - t0
+    return d
+
+
+def query_for(hs, d, seed):
+    return hs.Query(sources=d["sources"], mode=hs.HSAW_EDGE, k=d["k"], sampling=hs.HSAW_STOP_RULE, eps=d["eps"],
+                    seed=seed)
+
+
+def cpu_baseline(d, seed, seconds):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+    import oracle
+    t0 = time.time()
+    og = oracle.Graph(d["n"], d["src"], d["dst"], d["w"])
+    build_s = time.time() - t0
+    q = oracle.Query(og, d["sources"], seed=seed)
+    cal = oracle.Stream(q)
+    t0 = time.time()
+    cal.extend(1 << 62, max_attempts=20_000)
+    rate = 20_000 / max(time.time() - t0, 1e-6)
+    attempts = max(20_000, int(rate * seconds))
+    st = oracle.Stream(q)
+    t0 = time.time()
+    st.extend(1 << 62, max_attempts=attempts)
+    dt = time.time() - t0
+    return {"value": len(st) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {attempts} attempts of the same query stream ({len(st)} HSAWs, {dt:.1f} s, "
+                      f"oracle graph build {build_s:.0f} s untimed)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle timed on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    d = make_workload(args.scale)
+    og = oracle.Graph(d["n"], d["src"], d["dst"], d["w"])
+    q = oracle.Query(og, d["sources"], seed=synth.SEED_WALKS)
+    per_step = args.ref_attempts
+    st = oracle.Stream(q)
+    for _ in range(args.warmup):
+        st.extend(1 << 62, max_attempts=max(1000, per_step // 10))
+    hits0 = len(st)
+    t0 = time.time()
+    for _ in range(args.steps):
+        st.extend(1 << 62, max_attempts=per_step)
+    dt = time.time() - t0
+    v = (len(st) - hits0) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} attempts per step of the query stream"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hsaw", choices=["hsaw", "reference"])
+    ap.add_argument("--scale", type=int, default=26)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-attempts", type=int, default=400_000)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1702_05854_gb300 as hs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    d = make_workload(args.scale)
+    seed = synth.SEED_WALKS + rank
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g = hs.hsaw_graph_from_edges(d["n"], d["src"], d["dst"], d["w"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ingest_s = e0.elapsed_time(e1) / 1e3
+    q = query_for(hs, d, seed)
+
+    for _ in range(args.warmup):
+        hs.hsaw_solve(g, q)
+
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    hs.hsaw_profile_enable(True)
+    hits = 0
+    rounds = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        ids, gains, r = hs.hsaw_solve(g, q)
+        hits += r["hits"]
+        rounds.append(r["rounds_t"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    prof = hs.hsaw_profile_read()
+    hs.hsaw_profile_enable(False)
+    ck = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        h = torch.tensor([hits], dtype=torch.float64, device="cuda")
+        dist.all_reduce(h)
+        hits_all = float(h.item())
+    else:
+        hits_all = float(hits)
+    value = hits_all / elapsed
+
+    # roofline of the dominant kernel (the sampler): algorithmic bytes per launch / launch time
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    launches = max(prof["sampler_launches"], 1)
+    avg_launch_s = prof["sampler_ms"] / 1e3 / launches
+    bytes_per_launch = BYTES_PER_STEP * prof["sampler_steps"] / launches
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    traffic = None
+    per_attempt = NCU_TRAFFIC.get(sampler_hash())
+    if per_attempt is not None:
+        traffic = per_attempt * prof["sampler_attempts"] / launches
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_sample", "peak_source": "measured" if peaks else "fallback",
+                "sampler_share_of_step": prof["sampler_ms"] / 1e3 / elapsed,
+                "steps_per_s": prof["sampler_steps"] / (prof["sampler_ms"] / 1e3) if prof["sampler_ms"] else 0.0}
+
+    # end to end through the C ABI with host buffers: graph ingest from host arrays + solve
+    e2e = None
+    if args.e2e_steps > 0:
+        h2d = int(d["src"].nbytes + d["dst"].nbytes + d["w"].nbytes + d["sources"].nbytes)
+        d2h = d["k"] * 12
+        e_hits = 0
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            g2 = hs.hsaw_graph_from_edges(d["n"], d["src"], d["dst"], d["w"])
+            ids, gains, r = hs.hsaw_solve(g2, q)
+            e_hits += r["hits"]
+            g2.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        et = e0.elapsed_time(e1) / 1e3
+        e2e = {"value": e_hits * (world if dist else 1) / et, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "what": "hsaw_graph_from_edges(host edge list) + hsaw_solve per step"}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(d, seed, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"],
+                   "eps": d["eps"], "delta": "1/n", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (9.6 GB graph)", "hits_per_step": hits / args.steps,
+                   "rounds_t": rounds[-1], "graph_gen_s": d["gen_s"], "graph_ingest_s": ingest_s},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["kernel_launches"],
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

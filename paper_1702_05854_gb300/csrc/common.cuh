@@ -1,0 +1,143 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/hsaw.h"
+
+namespace hsaw {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+hsaw_status fail(hsaw_status st, const std::string& msg);
+hsaw_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define HSAW_CK(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) return ::hsaw::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HSAW_TRY(expr)                 \
+  do {                                 \
+    hsaw_status s_ = (expr);           \
+    if (s_ != HSAW_OK) return s_;      \
+  } while (0)
+
+// ------------------------------------------------------------------ device memory
+// Stream-ordered allocations from the device's default memory pool; freed blocks stay
+// cached in the pool (release threshold raised at first use), so per-call temporaries
+// cost no driver round trip after warm-up.
+hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+template <typename T>
+struct DBuf {  // grow-only device buffer
+  T* p = nullptr;
+  size_t cap = 0;  // elements
+  hsaw_status ensure(size_t n, cudaStream_t s, bool keep = false) {
+    if (n <= cap) return HSAW_OK;
+    size_t nc = cap ? cap : 1024;
+    while (nc < n) nc *= 2;
+    void* np = nullptr;
+    HSAW_TRY(dmalloc(&np, nc * sizeof(T), s));
+    if (keep && p && cap) HSAW_CK(cudaMemcpyAsync(np, p, cap * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    dfree(p, s);
+    p = static_cast<T*>(np);
+    cap = nc;
+    return HSAW_OK;
+  }
+  void release(cudaStream_t s) {
+    dfree(p, s);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// ------------------------------------------------------------------ graph
+// Device in-adjacency (Sec. 2.1).  node[v] = {first in-edge, in-degree, uniform weight
+// (0 if the in-weights differ), in-sum}; edge[e] = {tail node u of (u, v), running sum of
+// v's in-weights through e}.  In-edge j of v is live for a draw r iff
+// thr[j-1] <= r < thr[j]; none is live when r >= in-sum.
+struct Graph {
+  int64_t n = 0, m = 0;
+  uint4* node = nullptr;
+  uint2* edge = nullptr;
+  int64_t* input_index = nullptr;  // CSR position -> input edge index (NULL = identity)
+  int device = 0;
+};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: 10 rounds of two 32x32->64 multiplies with the
+// published multipliers, key bumped by the published Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Draw of node v in attempt a (one live-edge world per attempt).
+__device__ __forceinline__ uint4 node_draw(uint64_t a, uint32_t v, uint32_t k0, uint32_t k1) {
+  return philox4x32_10(make_uint4((uint32_t)a, (uint32_t)(a >> 32), v, 0u), k0, k1);
+}
+// Start node of attempt a: floor(x0 * n / 2^32).
+__device__ __forceinline__ uint32_t start_node(uint64_t a, uint32_t n, uint32_t k0, uint32_t k1) {
+  const uint4 x = philox4x32_10(make_uint4((uint32_t)a, (uint32_t)(a >> 32), 0u, 1u), k0, k1);
+  return __umulhi(x.x, n);
+}
+__device__ __forceinline__ bool source_coin(uint32_t x1, uint32_t p32) {
+  return p32 == 0xFFFFFFFFu || x1 < p32;
+}
+// Live in-edge index j in [0, deg) of a node with record nd for draw r < nd.w (in-sum).
+__device__ __forceinline__ uint32_t pick_in_edge(const uint2* __restrict__ edge, uint4 nd, uint32_t r) {
+  if (nd.z) return r / nd.z;  // equal weights: thr[j] = (j+1) w
+  uint32_t lo = 0, hi = nd.y;  // first j with r < thr[j]
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint32_t t = __ldg(&edge[nd.x + mid].y);
+    if (r < t) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------ primitives (primitives.cu)
+// Exclusive prefix sum in place; *total (device, may be NULL) receives the sum.
+hsaw_status exclusive_scan_u32(uint32_t* d, size_t n, uint32_t* total, cudaStream_t s);
+hsaw_status exclusive_scan_u64(uint64_t* d, size_t n, uint64_t* total, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the key.  The
+// result ends in (keys, vals) or (keys_alt, vals_alt); *in_alt tells which.
+hsaw_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
+                             int bits, cudaStream_t s, bool* in_alt);
+int bit_width(uint64_t x);  // bits needed for values in [0, x]
+
+// ------------------------------------------------------------------ launch helpers
+inline unsigned grid_for(size_t n, unsigned block, unsigned cap = 1u << 30) {
+  size_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+int sm_count();
+
+// Launch accounting (profiling): every kernel launch of the library calls count_launch();
+// sampler launches are bracketed by profile_begin / profile_end.
+void count_launch();
+void* profile_begin(cudaStream_t s);
+void profile_end(void* token, cudaStream_t s, uint64_t attempts);
+void profile_add_steps(uint64_t steps);
+
+}  // namespace hsaw
+
+// Opaque handle types of the ABI.
+struct hsaw_graph_s {
+  hsaw::Graph g;
+};

@@ -1,0 +1,459 @@
+// Occurrence counting, inverted index, greedy max-coverage and out-of-sample coverage
+// over the ordered HSAW stream (Alg. 4 / 7 "Greedy", Alg. 5 line 2 "Cov_{R'_t}").
+//
+// The walk elements of a range of walks are sorted by element id with their entry
+// positions (stable radix sort): the runs give the touched elements in increasing id
+// with their occurrence counts, and the run contents are the inverted index element ->
+// walks.  Greedy runs k rounds in ONE cooperative launch: a grid-wide argmax of
+// (count, -index) packed in 64 bits (ties to the smallest id), then the picked
+// element's uncovered walks are marked and every element of those walks is decremented.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "solver.cuh"
+
+namespace hsaw {
+
+enum : uint32_t { GS_BARRIER_TIMEOUT = 1u };
+
+void Cover::release(cudaStream_t s) {
+  keys.release(s); vals.release(s); keys2.release(s); vals2.release(s); run_flag.release(s);
+  uid.release(s); cnt.release(s); inv_off.release(s); inv_walk.release(s); entry_uidx.release(s);
+  walk_eoff.release(s); cnt_work.release(s); covered.release(s); allowed.release(s); partial.release(s);
+  misc.release(s);
+}
+
+// entry offsets of walks [first, first + count) relative to the first walk's first entry
+__global__ void k_walk_eoff(const int64_t* __restrict__ node_off, int64_t first, int64_t count, int edge_mode,
+                            uint32_t* __restrict__ eoff) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= count; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = first + i;
+    const int64_t b0 = node_off[first] - (edge_mode ? first : 0);
+    eoff[i] = (uint32_t)(node_off[j] - (edge_mode ? j : 0) - b0);
+  }
+}
+
+__global__ void k_keys_iota(const int32_t* __restrict__ el, uint32_t E, uint32_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < E; p += gridDim.x * blockDim.x) {
+    keys[p] = (uint32_t)el[p];
+    vals[p] = p;
+  }
+}
+
+__global__ void k_walk_of_entry(const uint32_t* __restrict__ eoff, uint32_t count, uint32_t* __restrict__ wof) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    for (uint32_t p = eoff[i]; p < eoff[i + 1]; ++p) wof[p] = i;
+}
+
+__global__ void k_run_flags(const uint32_t* __restrict__ skeys, uint32_t E, uint32_t* __restrict__ flag) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E; q += gridDim.x * blockDim.x)
+    flag[q] = (q == 0 || skeys[q] != skeys[q - 1]) ? 1u : 0u;
+}
+
+// excl = exclusive scan of the run flags
+__global__ void k_runs(const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
+                       const uint32_t* __restrict__ excl, const uint32_t* __restrict__ wof, uint32_t E,
+                       int32_t* __restrict__ uid, uint32_t* __restrict__ inv_off, uint32_t* __restrict__ inv_walk,
+                       uint32_t* __restrict__ entry_uidx) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E; q += gridDim.x * blockDim.x) {
+    const bool start = (q == 0 || skeys[q] != skeys[q - 1]);
+    const uint32_t r = excl[q] + (start ? 1u : 0u) - 1u;
+    if (start) {
+      uid[r] = (int32_t)skeys[q];
+      inv_off[r] = q;
+    }
+    const uint32_t p = svals[q];
+    inv_walk[q] = wof[p];
+    entry_uidx[p] = r;
+  }
+}
+
+__global__ void k_counts(const uint32_t* __restrict__ inv_off, uint32_t U, uint32_t* __restrict__ cnt) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < U; r += gridDim.x * blockDim.x)
+    cnt[r] = inv_off[r + 1] - inv_off[r];
+}
+
+hsaw_status cover_build(const Stream& st, hsaw_mode mode, int64_t first, int64_t count, Cover& cv, cudaStream_t s) {
+  cv.walks = count;
+  cv.entries = 0;
+  cv.unique = 0;
+  if (count <= 0) return HSAW_OK;
+  if (first < 0 || first + count > st.count) return fail(HSAW_E_INVALID, "cover: walk range outside the stream");
+  const bool em = (mode == HSAW_EDGE);
+  int64_t nb[2];
+  HSAW_CK(cudaMemcpyAsync(&nb[0], st.node_off.p + first, 8, cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaMemcpyAsync(&nb[1], st.node_off.p + first + count, 8, cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  const int64_t E64 = em ? (nb[1] - (first + count)) - (nb[0] - first) : nb[1] - nb[0];
+  if (E64 >= 0xFFFFFFFFll || count >= 0xFFFFFFFFll) return fail(HSAW_E_INVALID, "cover: too many walk elements");
+  const uint32_t E = (uint32_t)E64;
+  cv.entries = E;
+  HSAW_TRY(cv.walk_eoff.ensure((size_t)count + 1, s));
+  count_launch();
+  k_walk_eoff<<<grid_for((size_t)count + 1, 256, 8192), 256, 0, s>>>(st.node_off.p, first, count, em ? 1 : 0,
+                                                                      cv.walk_eoff.p);
+  HSAW_CK(cudaGetLastError());
+  if (E == 0) return HSAW_OK;
+  const int32_t* el = em ? st.edges.p + (nb[0] - first) : st.nodes.p + nb[0];
+  HSAW_TRY(cv.keys.ensure(E, s));
+  HSAW_TRY(cv.vals.ensure(E, s));
+  HSAW_TRY(cv.keys2.ensure(E, s));
+  HSAW_TRY(cv.vals2.ensure(E, s));
+  HSAW_TRY(cv.run_flag.ensure((size_t)E + 1, s));
+  HSAW_TRY(cv.inv_walk.ensure(E, s));
+  HSAW_TRY(cv.entry_uidx.ensure(E, s));
+  count_launch();
+  k_keys_iota<<<grid_for(E, 256, 8192), 256, 0, s>>>(el, E, cv.keys.p, cv.vals.p);
+  HSAW_CK(cudaGetLastError());
+  // the largest element id bounds the sort width
+  bool alt = false;
+  HSAW_TRY(radix_sort_pairs(cv.keys.p, cv.vals.p, cv.keys2.p, cv.vals2.p, E, 31, s, &alt));
+  uint32_t* sk = alt ? cv.keys2.p : cv.keys.p;
+  uint32_t* sv = alt ? cv.vals2.p : cv.vals.p;
+  uint32_t* wof = alt ? cv.keys.p : cv.keys2.p;  // the free pair member
+  count_launch();
+  k_walk_of_entry<<<grid_for(count, 128, 8192), 128, 0, s>>>(cv.walk_eoff.p, (uint32_t)count, wof);
+  HSAW_CK(cudaGetLastError());
+  count_launch();
+  k_run_flags<<<grid_for(E, 256, 8192), 256, 0, s>>>(sk, E, cv.run_flag.p);
+  HSAW_CK(cudaGetLastError());
+  HSAW_TRY(exclusive_scan_u32(cv.run_flag.p, E, cv.run_flag.p + E, s));
+  uint32_t U = 0;
+  HSAW_CK(cudaMemcpyAsync(&U, cv.run_flag.p + E, 4, cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  cv.unique = U;
+  HSAW_TRY(cv.uid.ensure(U, s));
+  HSAW_TRY(cv.inv_off.ensure((size_t)U + 1, s));
+  HSAW_TRY(cv.cnt.ensure(U, s));
+  count_launch();
+  k_runs<<<grid_for(E, 256, 8192), 256, 0, s>>>(sk, sv, cv.run_flag.p, wof, E, cv.uid.p, cv.inv_off.p, cv.inv_walk.p,
+                                                  cv.entry_uidx.p);
+  HSAW_CK(cudaGetLastError());
+  HSAW_CK(cudaMemcpyAsync(cv.inv_off.p + U, &E, 4, cudaMemcpyHostToDevice, s));
+  count_launch();
+  k_counts<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.inv_off.p, U, cv.cnt.p);
+  HSAW_CK(cudaGetLastError());
+  HSAW_CK(cudaStreamSynchronize(s));  // E lives on the host stack
+  return HSAW_OK;
+}
+
+// ------------------------------------------------------------------ greedy
+struct GreedyParams {
+  uint32_t U;
+  int32_t k;
+  uint32_t* cnt;  // running marginal counts
+  const uint32_t* inv_off;
+  const uint32_t* inv_walk;
+  const uint32_t* walk_eoff;
+  const uint32_t* entry_uidx;
+  uint8_t* covered;
+  uint8_t* allowed;
+  unsigned long long* partial;  // gridDim.x
+  uint32_t* out_u;
+  uint32_t* out_gain;
+  uint32_t* ctl;  // [0] barrier count, [1] barrier generation, [2] status, [3] rounds done
+};
+
+__device__ __forceinline__ void grid_barrier(uint32_t* ctl, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* vstatus = ctl + 2;
+    if (!(*vstatus & GS_BARRIER_TIMEOUT)) {
+      volatile uint32_t* vgen = ctl + 1;
+      const uint32_t g = *vgen;
+      __threadfence();
+      const uint32_t arrived = atomicAdd(ctl, 1u);
+      if (arrived == nblocks - 1) {
+        atomicExch(ctl, 0u);
+        __threadfence();
+        atomicAdd(ctl + 1, 1u);
+      } else {
+        uint32_t spins = 0;
+        while (*vgen == g) {
+          __nanosleep(100);
+          if (++spins > (1u << 24)) {  // ~2 s: record and stop waiting
+            atomicOr(ctl + 2, GS_BARRIER_TIMEOUT);
+            break;
+          }
+          if (*vstatus & GS_BARRIER_TIMEOUT) break;
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long y = __shfl_down_sync(0xffffffffu, v, o);
+    v = y > v ? y : v;
+  }
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      unsigned long long y = __shfl_down_sync(0xffffffffu, v, o);
+      v = y > v ? y : v;
+    }
+    if (lane == 0) sm[32] = v;
+  }
+  __syncthreads();
+  return sm[32];
+}
+
+__global__ void __launch_bounds__(512) k_greedy(GreedyParams P) {
+  __shared__ unsigned long long sm[33];
+  const unsigned G = gridDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t gsz = (size_t)G * blockDim.x;
+  int32_t r = 0;
+  for (; r < P.k; ++r) {
+    unsigned long long best = 0;
+    for (size_t u = gtid; u < P.U; u += gsz) {
+      // counts, flags and partials change across blocks between barriers: read them from L2
+      if (__ldcg(&P.allowed[u])) {
+        const unsigned long long key = ((unsigned long long)__ldcg(&P.cnt[u]) << 32) | (0xFFFFFFFFu - (uint32_t)u);
+        best = key > best ? key : best;
+      }
+    }
+    best = block_max_u64(best, sm);
+    if (threadIdx.x == 0) P.partial[blockIdx.x] = best;
+    grid_barrier(P.ctl, G);
+    best = 0;
+    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
+      const unsigned long long x = __ldcg(&P.partial[b]);
+      best = x > best ? x : best;
+    }
+    best = block_max_u64(best, sm);
+    const uint32_t gain = (uint32_t)(best >> 32);
+    if (gain == 0) break;  // every remaining gain is zero (same decision in every block)
+    const uint32_t u = 0xFFFFFFFFu - (uint32_t)best;
+    if (gtid == 0) {
+      P.out_u[r] = u;
+      P.out_gain[r] = gain;
+      P.allowed[u] = 0;
+    }
+    const uint32_t q0 = P.inv_off[u], q1 = P.inv_off[u + 1];
+    for (size_t q = q0 + gtid; q < q1; q += gsz) {
+      const uint32_t j = P.inv_walk[q];
+      if (!__ldcg(&P.covered[j])) {
+        P.covered[j] = 1;
+        for (uint32_t p = P.walk_eoff[j]; p < P.walk_eoff[j + 1]; ++p) atomicSub(&P.cnt[P.entry_uidx[p]], 1u);
+      }
+    }
+    grid_barrier(P.ctl, G);
+  }
+  if (gtid == 0) P.ctl[3] = (uint32_t)r;
+}
+
+__global__ void k_allowed(const int32_t* __restrict__ uid, uint32_t U, const uint8_t* __restrict__ cand,
+                          uint8_t* __restrict__ allowed) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
+    allowed[u] = cand ? (cand[uid[u]] ? 1 : 0) : 1;
+}
+
+__global__ void k_pick_ids(const uint32_t* __restrict__ out_u, const int32_t* __restrict__ uid, int32_t r,
+                           int64_t* __restrict__ ids) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x) ids[i] = uid[out_u[i]];
+}
+
+__global__ void k_mark_bits(const int64_t* __restrict__ ids, int32_t r, uint32_t* __restrict__ bits) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x)
+    atomicOr(&bits[ids[i] >> 5], 1u << (ids[i] & 31));
+}
+
+// Zero-gain picks: the smallest ids of C not picked yet, in increasing order (one block).
+__global__ void __launch_bounds__(1024) k_zero_fill(int64_t M, const uint8_t* __restrict__ cand,
+                                                    const uint32_t* __restrict__ picked_bits, int32_t r0, int32_t k,
+                                                    int64_t* __restrict__ ids, uint32_t* __restrict__ gains) {
+  __shared__ int32_t warp_cnt[32];
+  __shared__ int32_t filled;
+  if (threadIdx.x == 0) filled = r0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t base = 0; base < M; base += blockDim.x) {
+    if (filled >= k) break;
+    const int64_t x = base + threadIdx.x;
+    const bool ok = x < M && (!cand || cand[x]) && !((picked_bits[x >> 5] >> (x & 31)) & 1u);
+    const unsigned b = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) warp_cnt[w] = __popc(b);
+    __syncthreads();
+    int32_t before = 0;
+    for (int i = 0; i < w; ++i) before += warp_cnt[i];
+    const int32_t pos = filled + before + __popc(b & ((1u << lane) - 1u));
+    if (ok && pos < k) {
+      ids[pos] = x;
+      gains[pos] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int32_t tot = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += warp_cnt[i];
+      filled += tot;
+    }
+    __syncthreads();
+  }
+}
+
+static int greedy_grid() {
+  static int cached = 0;
+  if (!cached) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_greedy, 512, 0);
+    cached = std::max(1, std::min(b, 2)) * sm_count();
+  }
+  return cached;
+}
+
+hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t k, int64_t* ids_host,
+                         uint32_t* gains_host, cudaStream_t s) {
+  if (k < 1) return fail(HSAW_E_INVALID, "greedy: k < 1");
+  const uint32_t U = (uint32_t)cv.unique;
+  DBuf<int64_t> ids;
+  DBuf<uint32_t> outs;  // out_u[k], out_gain[k]
+  HSAW_TRY(ids.ensure(k, s));
+  HSAW_TRY(outs.ensure((size_t)2 * k + 8, s));
+  uint32_t* ctl = outs.p + 2 * (size_t)k;
+  HSAW_CK(cudaMemsetAsync(ctl, 0, 8 * sizeof(uint32_t), s));
+  int32_t rounds = 0;
+  hsaw_status st = HSAW_OK;
+  if (U > 0 && cv.walks > 0) {
+    const int G = greedy_grid();
+    HSAW_TRY(cv.cnt_work.ensure(U, s));
+    HSAW_TRY(cv.allowed.ensure(U, s));
+    HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
+    HSAW_TRY(cv.partial.ensure(G, s));
+    HSAW_CK(cudaMemcpyAsync(cv.cnt_work.p, cv.cnt.p, (size_t)U * 4, cudaMemcpyDeviceToDevice, s));
+    HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
+    count_launch();
+    k_allowed<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, U, cand_dev, cv.allowed.p);
+    HSAW_CK(cudaGetLastError());
+    GreedyParams P;
+    P.U = U;
+    P.k = k;
+    P.cnt = cv.cnt_work.p;
+    P.inv_off = cv.inv_off.p;
+    P.inv_walk = cv.inv_walk.p;
+    P.walk_eoff = cv.walk_eoff.p;
+    P.entry_uidx = cv.entry_uidx.p;
+    P.covered = cv.covered.p;
+    P.allowed = cv.allowed.p;
+    P.partial = cv.partial.p;
+    P.out_u = outs.p;
+    P.out_gain = outs.p + k;
+    P.ctl = ctl;
+    void* args[] = {&P};
+    count_launch();
+    HSAW_CK(cudaLaunchCooperativeKernel((const void*)k_greedy, dim3(G), dim3(512), args, 0, s));
+    uint32_t h[4];
+    HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
+    HSAW_CK(cudaStreamSynchronize(s));
+    if (h[2] & GS_BARRIER_TIMEOUT) st = fail(HSAW_E_DEVICE, "greedy: grid barrier timed out");
+    rounds = (int32_t)h[3];
+    if (st == HSAW_OK && rounds > 0) {
+      count_launch();
+      k_pick_ids<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(outs.p, cv.uid.p, rounds, ids.p);
+      if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: id launch failed");
+    }
+  }
+  if (st == HSAW_OK && rounds < k) {
+    uint32_t* bits = nullptr;
+    const size_t words = (size_t)(M + 31) / 32;
+    st = dmalloc((void**)&bits, words * 4, s);
+    if (st == HSAW_OK) {
+      cudaMemsetAsync(bits, 0, words * 4, s);
+      if (rounds > 0) { count_launch(); k_mark_bits<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(ids.p, rounds, bits); }
+      count_launch();
+      k_zero_fill<<<1, 1024, 0, s>>>(M, cand_dev, bits, rounds, k, ids.p, outs.p + k);
+      if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: zero-fill launch failed");
+      dfree(bits, s);
+    }
+  }
+  if (st == HSAW_OK) {
+    if (ids_host) cudaMemcpyAsync(ids_host, ids.p, (size_t)k * 8, cudaMemcpyDeviceToHost, s);
+    if (gains_host) cudaMemcpyAsync(gains_host, outs.p + k, (size_t)k * 4, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: result copy failed");
+  }
+  ids.release(s);
+  outs.release(s);
+  return st;
+}
+
+// ------------------------------------------------------------------ coverage on R'_t
+__global__ void k_cover_count(const int64_t* __restrict__ node_off, const int32_t* __restrict__ nodes,
+                              const int32_t* __restrict__ edges, int edge_mode, int64_t first, int64_t count,
+                              const uint32_t* __restrict__ T_sorted, int32_t k, unsigned long long* __restrict__ cov) {
+  unsigned long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = first + i;
+    const int64_t b = node_off[j] - (edge_mode ? j : 0), e = node_off[j + 1] - (edge_mode ? j + 1 : 0);
+    const int32_t* el = edge_mode ? edges : nodes;
+    for (int64_t p = b; p < e; ++p) {
+      const uint32_t x = (uint32_t)el[p];
+      int32_t lo = 0, hi = k;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (T_sorted[mid] < x) lo = mid + 1; else hi = mid;
+      }
+      if (lo < k && T_sorted[lo] == x) { ++c; break; }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cov, c);
+}
+
+__global__ void k_ids_to_keys(const int64_t* __restrict__ T, int32_t k, uint32_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    keys[i] = (uint32_t)T[i];
+    vals[i] = (uint32_t)i;
+  }
+}
+
+hsaw_status cover_count(const Stream& st, hsaw_mode mode, int64_t first, int64_t count, const int64_t* T, int32_t k,
+                        uint64_t* cov, cudaStream_t s) {
+  *cov = 0;
+  if (count <= 0 || k <= 0) return HSAW_OK;
+  if (first < 0 || first + count > st.count) return fail(HSAW_E_INVALID, "coverage: walk range outside the stream");
+  uint32_t* buf = nullptr;
+  HSAW_TRY(dmalloc((void**)&buf, (size_t)4 * k * 4 + 64, s));
+  int64_t* dT = nullptr;
+  hsaw_status stt = dmalloc((void**)&dT, (size_t)k * 8, s);
+  if (stt != HSAW_OK) { dfree(buf, s); return stt; }
+  uint32_t *k1 = buf, *v1 = buf + k, *k2 = buf + 2 * (size_t)k, *v2 = buf + 3 * (size_t)k;
+  unsigned long long* dcov = (unsigned long long*)(buf + 4 * (size_t)k + 2);
+  dcov = (unsigned long long*)(((uintptr_t)dcov + 7) & ~(uintptr_t)7);
+  cudaMemcpyAsync(dT, T, (size_t)k * 8, cudaMemcpyHostToDevice, s);
+  count_launch();
+  k_ids_to_keys<<<grid_for(k, 256, 1024), 256, 0, s>>>(dT, k, k1, v1);
+  bool alt = false;
+  stt = radix_sort_pairs(k1, v1, k2, v2, (size_t)k, 31, s, &alt);
+  if (stt == HSAW_OK) {
+    cudaMemsetAsync(dcov, 0, 8, s);
+    count_launch();
+    k_cover_count<<<grid_for(count, 256, 8192), 256, 0, s>>>(st.node_off.p, st.nodes.p, st.edges.p,
+                                                             mode == HSAW_EDGE ? 1 : 0, first, count,
+                                                             alt ? k2 : k1, k, dcov);
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, dcov, 8, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      stt = fail(HSAW_E_DEVICE, "coverage kernel failed");
+    *cov = h;
+  }
+  dfree(buf, s);
+  dfree(dT, s);
+  return stt;
+}
+
+}  // namespace hsaw

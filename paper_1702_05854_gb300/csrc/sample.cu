@@ -1,0 +1,457 @@
+// HSAW sampling (Sec. 4, Alg. 1-3) on sm_103a.
+//
+// Attempt a is one live-edge world: node v's live in-edge and source coin come from
+// Philox(seed; a, v), so a walk is a trajectory of a functional graph and Brent's cycle
+// detection (Sec. 4.2.2) is exact in O(1) space per walk.  A persistent warp claims
+// chunks of consecutive attempts; lanes that finish take the next attempt of the warp's
+// chunk cursor at once (no lane waits for the warp's longest walk).  Hits are recorded
+// per chunk as (attempt offset, length); the compaction kernel orders each chunk's hits
+// by attempt id and places them by an exclusive scan over chunks, so the stream is
+// ordered by attempt id regardless of which warp ran what.  Hit walks are then
+// re-derived from their attempt id (the paper's <Seed_h, Len_h> path encoding) straight
+// into the flat walk buffers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "solver.cuh"
+
+namespace hsaw {
+
+enum : uint32_t { ST_OVERFLOW = 1u, ST_STEP_CAP = 2u };
+
+struct SampleParams {
+  const uint4* __restrict__ node;
+  const uint2* __restrict__ edge;
+  const uint32_t* __restrict__ s_bits;
+  const uint32_t* __restrict__ p32;
+  const uint8_t* __restrict__ edge_removed;
+  const uint8_t* __restrict__ node_removed;
+  uint32_t n;
+  uint32_t k0, k1;
+  uint64_t a0;           // first attempt of this launch
+  uint32_t n_attempts;   // attempts in this launch
+  uint32_t chunk;        // attempts per chunk
+  uint32_t n_chunks;
+  uint32_t cap;          // hit records per chunk
+  uint32_t step_cap;
+  uint32_t* chunk_ctr;   // [0] work counter, [1] status bits
+  uint32_t* chunk_hits;  // n_chunks
+  uint2* recs;           // n_chunks * cap
+  unsigned long long* steps;
+};
+
+template <bool HAS_P, bool HAS_REM>
+__global__ void __launch_bounds__(256) k_sample(SampleParams P) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t cur = 0, cur_end = 0;  // warp's attempt cursor within the launch
+  bool more = true;
+  bool active = false;
+  uint32_t off = 0, v = 0, tort = 0, power = 1, lam = 0, len = 0;
+  unsigned long long my_steps = 0;
+  for (;;) {
+    unsigned need = __ballot_sync(FULL, !active);
+    while (need) {
+      if (cur >= cur_end) {
+        if (!more) break;
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(P.chunk_ctr, 1u);
+        c = __shfl_sync(FULL, c, 0);
+        if (c >= P.n_chunks) { more = false; break; }
+        cur = c * P.chunk;
+        cur_end = min(cur + P.chunk, P.n_attempts);
+      }
+      const uint32_t avail = cur_end - cur;
+      const uint32_t rank = __popc(need & lt);
+      if (!active && rank < avail) {
+        off = cur + rank;
+        const uint64_t a = P.a0 + off;
+        v = start_node(a, P.n, P.k0, P.k1);
+        tort = v;
+        power = 1;
+        lam = 0;
+        len = 1;
+        active = true;
+      }
+      cur += min((uint32_t)__popc(need), avail);
+      need = __ballot_sync(FULL, !active);
+    }
+    if (!__any_sync(FULL, active)) break;
+    if (active) {
+      // one step of the walk at node v (Alg. 1 lines 5-13)
+      const uint64_t a = P.a0 + off;
+      int outcome = -1;  // -1 continue, 0 miss, 1 hit
+      if (HAS_REM && len == 1 && P.node_removed && P.node_removed[v]) outcome = 0;
+      if (outcome < 0) {
+        const uint32_t sw = __ldg(&P.s_bits[v >> 5]);
+        const uint4 nd = __ldg(&P.node[v]);
+        const bool suspect = (sw >> (v & 31)) & 1u;
+        if (!HAS_P && suspect) {
+          outcome = 1;
+        } else {
+          const uint4 x = node_draw(a, v, P.k0, P.k1);
+          if (HAS_P && suspect && source_coin(x.y, __ldg(&P.p32[v]))) {
+            outcome = 1;
+          } else if (++my_steps, x.x >= nd.w) {
+            outcome = 0;  // no live in-edge
+          } else {
+            const uint32_t e = nd.x + pick_in_edge(P.edge, nd, x.x);
+            const uint32_t u = __ldg(&P.edge[e].x);
+            if (HAS_REM && ((P.edge_removed && P.edge_removed[e]) || (P.node_removed && P.node_removed[u]))) {
+              outcome = 0;
+            } else if (u == tort) {
+              outcome = 0;  // Brent: the walk closed a cycle
+            } else {
+              if (++lam == power) {
+                tort = u;
+                power <<= 1;
+                lam = 0;
+              }
+              v = u;
+              if (++len > P.step_cap) {
+                atomicOr(P.chunk_ctr + 1, ST_STEP_CAP);
+                outcome = 0;
+              }
+            }
+          }
+        }
+      }
+      if (outcome >= 0) {
+        active = false;
+        if (outcome == 1) {
+          const uint32_t ck = off / P.chunk;
+          const uint32_t slot = atomicAdd(&P.chunk_hits[ck], 1u);
+          if (slot < P.cap) P.recs[(size_t)ck * P.cap + slot] = make_uint2(off, len);
+          else atomicOr(P.chunk_ctr + 1, ST_OVERFLOW);
+        }
+      }
+    }
+  }
+  // steps of this warp
+#pragma unroll
+  for (int o = 16; o; o >>= 1) my_steps += __shfl_down_sync(FULL, my_steps, o);
+  if (lane == 0 && my_steps) atomicAdd(P.steps, my_steps);
+}
+
+// Order each chunk's hits by attempt id and write them at the chunk's scanned offset.
+// One warp per chunk; rank = number of the chunk's records with a smaller offset.
+__global__ void k_compact(const uint32_t* __restrict__ chunk_hits, const uint32_t* __restrict__ chunk_off,
+                          const uint2* __restrict__ recs, uint32_t cap, uint32_t n_chunks, uint64_t a0,
+                          uint64_t* __restrict__ out_aid, uint32_t* __restrict__ out_len) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t ck = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ck < n_chunks; ck += warps) {
+    const uint32_t c = min(chunk_hits[ck], cap);
+    if (c == 0) continue;
+    const uint2* r = recs + (size_t)ck * cap;
+    const uint32_t base = chunk_off[ck];
+    for (uint32_t i = lane; i < c; i += 32) {
+      const uint2 me = r[i];
+      uint32_t rank = 0;
+      for (uint32_t j = 0; j < c; ++j) rank += (r[j].x < me.x) ? 1u : 0u;
+      out_aid[base + rank] = a0 + me.x;
+      out_len[base + rank] = me.y;
+    }
+  }
+}
+
+__global__ void k_clamp(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, uint32_t n, uint32_t cap) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = min(in[i], cap);
+}
+
+__global__ void k_len_to_u64(const uint32_t* __restrict__ len, int64_t n, uint64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = len[i];
+}
+
+__global__ void k_offsets(const uint64_t* __restrict__ excl, int64_t n, int64_t base, int64_t* __restrict__ node_off,
+                          const uint64_t* __restrict__ total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+    node_off[i] = base + (int64_t)(i < n ? excl[i] : *total);
+}
+
+// Re-derive hit walks from their attempt ids (path encoding) into the flat buffers.
+__global__ void k_rewalk(const uint4* __restrict__ node, const uint2* __restrict__ edge, uint32_t n, uint32_t k0,
+                         uint32_t k1, const uint64_t* __restrict__ aid, const uint32_t* __restrict__ len,
+                         const int64_t* __restrict__ node_off, int64_t h0, int64_t h1, int32_t* __restrict__ nodes,
+                         int32_t* __restrict__ edges) {
+  for (int64_t h = h0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < h1; h += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = aid[h];
+    const uint32_t l = len[h];
+    const int64_t nb = node_off[h], eb = nb - h;
+    uint32_t v = start_node(a, n, k0, k1);
+    nodes[nb] = (int32_t)v;
+    for (uint32_t i = 1; i < l; ++i) {
+      const uint4 x = node_draw(a, v, k0, k1);
+      const uint4 nd = __ldg(&node[v]);
+      const uint32_t e = nd.x + pick_in_edge(edge, nd, x.x);
+      const uint32_t u = __ldg(&edge[e].x);
+      nodes[nb + i] = (int32_t)u;
+      edges[eb + i - 1] = (int32_t)e;
+      v = u;
+    }
+  }
+}
+
+// Per-attempt outcome (0 no edge, 1 hit, 2 cycle, 3 removed) and nodes walked.
+template <bool HAS_P, bool HAS_REM>
+__global__ void k_classify(SampleParams P, uint64_t first, int64_t count, int8_t* __restrict__ outcome,
+                           int32_t* __restrict__ length) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = first + (uint64_t)i;
+    uint32_t v = start_node(a, P.n, P.k0, P.k1), tort = v, power = 1, lam = 0, len = 1;
+    int out = -1;
+    if (HAS_REM && P.node_removed && P.node_removed[v]) out = 3;
+    while (out < 0) {
+      const bool suspect = (__ldg(&P.s_bits[v >> 5]) >> (v & 31)) & 1u;
+      const uint4 x = node_draw(a, v, P.k0, P.k1);
+      if (suspect && (!HAS_P || source_coin(x.y, __ldg(&P.p32[v])))) { out = 1; break; }
+      const uint4 nd = __ldg(&P.node[v]);
+      if (x.x >= nd.w) { out = 0; break; }
+      const uint32_t e = nd.x + pick_in_edge(P.edge, nd, x.x);
+      const uint32_t u = __ldg(&P.edge[e].x);
+      if (HAS_REM && ((P.edge_removed && P.edge_removed[e]) || (P.node_removed && P.node_removed[u]))) { out = 3; break; }
+      if (u == tort) { out = 2; break; }
+      if (++lam == power) { tort = u; power <<= 1; lam = 0; }
+      v = u;
+      if (++len > P.step_cap) { atomicOr(P.chunk_ctr + 1, ST_STEP_CAP); out = 0; break; }
+    }
+    outcome[i] = (int8_t)out;
+    length[i] = (int32_t)len;
+  }
+}
+
+// ------------------------------------------------------------------ host
+__global__ void k_set_bits(const int32_t* __restrict__ src, const uint32_t* __restrict__ p, int32_t cnt,
+                           uint32_t* __restrict__ bits, uint32_t* __restrict__ p32) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)src[i];
+    atomicOr(&bits[v >> 5], 1u << (v & 31));
+    if (p32) p32[v] = p[i];
+  }
+}
+
+hsaw_status query_upload(const Graph& g, const hsaw_query* q, QueryDev& qd, cudaStream_t s) {
+  if (!q) return fail(HSAW_E_INVALID, "query: NULL");
+  if (q->n_sources < 1 || !q->sources) return fail(HSAW_E_INVALID, "query: need at least one source");
+  std::vector<uint8_t> seen((size_t)g.n, 0);
+  for (int32_t i = 0; i < q->n_sources; ++i) {
+    int32_t v = q->sources[i];
+    if (v < 0 || v >= g.n) return fail(HSAW_E_RANGE, "query: source outside [0, n)");
+    if (seen[v]) return fail(HSAW_E_INVALID, "query: duplicate source");
+    seen[v] = 1;
+  }
+  const size_t words = (size_t)(g.n + 31) / 32;
+  HSAW_TRY(dmalloc((void**)&qd.s_bits, words * 4, s));
+  HSAW_CK(cudaMemsetAsync(qd.s_bits, 0, words * 4, s));
+  if (q->p_fixed) {
+    HSAW_TRY(dmalloc((void**)&qd.p32, (size_t)g.n * 4, s));
+    HSAW_CK(cudaMemsetAsync(qd.p32, 0, (size_t)g.n * 4, s));
+  }
+  int32_t* d_src = nullptr;
+  uint32_t* d_p = nullptr;
+  HSAW_TRY(dmalloc((void**)&d_src, (size_t)q->n_sources * 4, s));
+  HSAW_CK(cudaMemcpyAsync(d_src, q->sources, (size_t)q->n_sources * 4, cudaMemcpyHostToDevice, s));
+  if (q->p_fixed) {
+    HSAW_TRY(dmalloc((void**)&d_p, (size_t)q->n_sources * 4, s));
+    HSAW_CK(cudaMemcpyAsync(d_p, q->p_fixed, (size_t)q->n_sources * 4, cudaMemcpyHostToDevice, s));
+  }
+  count_launch();
+  k_set_bits<<<grid_for(q->n_sources, 256, 1024), 256, 0, s>>>(d_src, d_p, q->n_sources, qd.s_bits, qd.p32);
+  HSAW_CK(cudaGetLastError());
+  dfree(d_src, s);
+  dfree(d_p, s);
+  qd.seed = q->seed;
+  return HSAW_OK;
+}
+
+void query_release(QueryDev& qd, cudaStream_t s) {
+  dfree(qd.s_bits, s);
+  dfree(qd.p32, s);
+  if (qd.owns_removed) {
+    dfree(qd.edge_removed, s);
+    dfree(qd.node_removed, s);
+  }
+  qd = QueryDev();
+}
+
+void Stream::release(cudaStream_t s) {
+  aid.release(s); len.release(s); node_off.release(s); nodes.release(s); edges.release(s);
+  chunk_hits.release(s); chunk_off.release(s); ctrs.release(s); recs.release(s); tmp64.release(s);
+}
+
+hsaw_status stream_init(Stream& st, uint64_t first_attempt, uint64_t max_attempts, cudaStream_t s) {
+  st.count = 0;
+  st.total_nodes = 0;
+  st.first_attempt = first_attempt;
+  st.next_attempt = first_attempt;
+  st.steps = 0;
+  st.max_attempts = max_attempts ? max_attempts : (1ull << 62);
+  HSAW_TRY(st.node_off.ensure(1024, s));
+  HSAW_CK(cudaMemsetAsync(st.node_off.p, 0, sizeof(int64_t), s));
+  HSAW_TRY(st.ctrs.ensure(8, s));
+  return HSAW_OK;
+}
+
+static SampleParams make_params(const Graph& g, const QueryDev& qd) {
+  SampleParams P{};
+  P.node = g.node;
+  P.edge = g.edge;
+  P.s_bits = qd.s_bits;
+  P.p32 = qd.p32;
+  P.edge_removed = qd.edge_removed;
+  P.node_removed = qd.node_removed;
+  P.n = (uint32_t)g.n;
+  P.k0 = (uint32_t)qd.seed;
+  P.k1 = (uint32_t)(qd.seed >> 32);
+  P.step_cap = (uint32_t)std::min<uint64_t>(4ull * (uint64_t)g.n + 64ull, 0xFFFFFFF0ull);
+  return P;
+}
+
+static int sample_blocks_per_sm() {
+  static int cached = 0;
+  if (!cached) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample<false, false>, 256, 0);
+    cached = b > 0 ? b : 1;
+  }
+  return cached;
+}
+
+static void launch_sample(const SampleParams& P, unsigned grid, cudaStream_t s) {
+  const bool hp = P.p32 != nullptr, hr = (P.edge_removed || P.node_removed);
+  if (hp && hr) { count_launch(); k_sample<true, true><<<grid, 256, 0, s>>>(P); }
+  else if (hp) { count_launch(); k_sample<true, false><<<grid, 256, 0, s>>>(P); }
+  else if (hr) { count_launch(); k_sample<false, true><<<grid, 256, 0, s>>>(P); }
+  else { count_launch(); k_sample<false, false><<<grid, 256, 0, s>>>(P); }
+}
+
+hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_t want, cudaStream_t s) {
+  SampleParams P = make_params(g, qd);
+  const uint32_t CHUNK = 256;
+  unsigned long long* d_steps = nullptr;
+  HSAW_TRY(st.tmp64.ensure(1, s));
+  while (st.count < want) {
+    const uint64_t used = st.next_attempt - st.first_attempt;
+    if (used >= st.max_attempts) return fail(HSAW_E_TIMEOUT, "sampling: attempt budget exhausted before enough hits");
+    // launch size from the hit rate so far (2^20 .. 2^28 attempts; doubling while no hit)
+    const double need = (double)(want - st.count);
+    st.hit_rate = used ? (double)st.count / (double)used : 0.0;
+    double target = st.hit_rate > 0 ? need / st.hit_rate * 1.05 + 4096.0 : std::max(1048576.0, 2.0 * (double)used);
+    target = std::max(target, 1048576.0);
+    target = std::min(target, 268435456.0);
+    uint64_t batch = (uint64_t)target;
+    batch = std::min<uint64_t>(batch, st.max_attempts - used);
+    batch = (batch + CHUNK - 1) / CHUNK * CHUNK;
+    const uint32_t n_chunks = (uint32_t)(batch / CHUNK);
+    // records per chunk: a few standard deviations above the expected hits, else all
+    double exp_hits = std::max(st.hit_rate, 0.0) * CHUNK;
+    uint32_t cap = (uint32_t)std::min<double>(CHUNK, std::ceil(exp_hits + 6.0 * std::sqrt(exp_hits + 1.0) + 8.0));
+    if (st.hit_rate == 0.0) cap = CHUNK;
+    for (int attempt_cap = 0; attempt_cap < 2; ++attempt_cap) {
+      HSAW_TRY(st.chunk_hits.ensure(n_chunks, s));
+      HSAW_TRY(st.chunk_off.ensure(n_chunks, s));
+      HSAW_TRY(st.recs.ensure((size_t)n_chunks * cap, s));
+      HSAW_CK(cudaMemsetAsync(st.chunk_hits.p, 0, (size_t)n_chunks * 4, s));
+      HSAW_CK(cudaMemsetAsync(st.ctrs.p, 0, 8 * 4, s));
+      d_steps = reinterpret_cast<unsigned long long*>(st.tmp64.p);
+      HSAW_CK(cudaMemsetAsync(d_steps, 0, 8, s));
+      P.a0 = st.next_attempt;
+      P.n_attempts = (uint32_t)batch;
+      P.chunk = CHUNK;
+      P.n_chunks = n_chunks;
+      P.cap = cap;
+      P.chunk_ctr = st.ctrs.p;
+      P.chunk_hits = st.chunk_hits.p;
+      P.recs = st.recs.p;
+      P.steps = d_steps;
+      const unsigned grid = (unsigned)std::max(1, std::min<int>(sm_count() * sample_blocks_per_sm(),
+                                                                 (int)((n_chunks + 7) / 8)));
+      void* prof = profile_begin(s);
+      launch_sample(P, grid, s);
+      profile_end(prof, s, batch);
+      HSAW_CK(cudaGetLastError());
+      count_launch();
+      k_clamp<<<grid_for(n_chunks, 256, 4096), 256, 0, s>>>(st.chunk_hits.p, st.chunk_off.p, n_chunks, cap);
+      HSAW_CK(cudaGetLastError());
+      HSAW_TRY(exclusive_scan_u32(st.chunk_off.p, n_chunks, st.ctrs.p + 2, s));
+      uint32_t h[4];
+      unsigned long long hs = 0;
+      HSAW_CK(cudaMemcpyAsync(h, st.ctrs.p, 16, cudaMemcpyDeviceToHost, s));
+      HSAW_CK(cudaMemcpyAsync(&hs, d_steps, 8, cudaMemcpyDeviceToHost, s));
+      HSAW_CK(cudaStreamSynchronize(s));
+      if (h[1] & ST_STEP_CAP) return fail(HSAW_E_STEP_CAP, "sampling: a walk exceeded its step guard");
+      if ((h[1] & ST_OVERFLOW) && cap < CHUNK) {
+        cap = CHUNK;  // rare: rerun this launch with room for every attempt to hit
+        continue;
+      }
+      const uint32_t new_hits = h[2];
+      st.steps += hs;
+      profile_add_steps(hs);
+      // append the ordered hits
+      HSAW_TRY(st.aid.ensure((size_t)st.count + new_hits, s, true));
+      HSAW_TRY(st.len.ensure((size_t)st.count + new_hits, s, true));
+      HSAW_TRY(st.node_off.ensure((size_t)st.count + new_hits + 1, s, true));
+      if (new_hits) {
+        count_launch();
+        k_compact<<<grid_for((size_t)n_chunks * 32, 256, 8192), 256, 0, s>>>(
+            st.chunk_hits.p, st.chunk_off.p, st.recs.p, cap, n_chunks, st.next_attempt, st.aid.p + st.count,
+            st.len.p + st.count);
+        HSAW_CK(cudaGetLastError());
+        HSAW_TRY(st.tmp64.ensure((size_t)new_hits + 1, s));
+        count_launch();
+        k_len_to_u64<<<grid_for(new_hits, 256, 4096), 256, 0, s>>>(st.len.p + st.count, new_hits, st.tmp64.p);
+        HSAW_CK(cudaGetLastError());
+        HSAW_TRY(exclusive_scan_u64(st.tmp64.p, new_hits, st.tmp64.p + new_hits, s));
+        count_launch();
+        k_offsets<<<grid_for((size_t)new_hits + 1, 256, 4096), 256, 0, s>>>(
+            st.tmp64.p, new_hits, st.total_nodes, st.node_off.p + st.count, st.tmp64.p + new_hits);
+        HSAW_CK(cudaGetLastError());
+        uint64_t added = 0;
+        HSAW_CK(cudaMemcpyAsync(&added, st.tmp64.p + new_hits, 8, cudaMemcpyDeviceToHost, s));
+        HSAW_CK(cudaStreamSynchronize(s));
+        const int64_t tot = st.total_nodes + (int64_t)added;
+        HSAW_TRY(st.nodes.ensure((size_t)tot, s, true));
+        HSAW_TRY(st.edges.ensure((size_t)tot, s, true));
+        count_launch();
+        k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, P.k0, P.k1, st.aid.p,
+                                                                     st.len.p, st.node_off.p, st.count,
+                                                                     st.count + new_hits, st.nodes.p, st.edges.p);
+        HSAW_CK(cudaGetLastError());
+        st.total_nodes = tot;
+        st.count += new_hits;
+      }
+      st.next_attempt += batch;
+      break;
+    }
+  }
+  return HSAW_OK;
+}
+
+hsaw_status classify_attempts(const Graph& g, const QueryDev& qd, uint64_t first, int64_t count, int8_t* outcome,
+                              int32_t* length, cudaStream_t s) {
+  SampleParams P = make_params(g, qd);
+  uint32_t* d_ctr = nullptr;
+  HSAW_TRY(dmalloc((void**)&d_ctr, 16, s));
+  HSAW_CK(cudaMemsetAsync(d_ctr, 0, 16, s));
+  P.chunk_ctr = d_ctr;
+  const unsigned grid = grid_for(count, 128, 1u << 16);
+  const bool hp = P.p32 != nullptr, hr = (P.edge_removed || P.node_removed);
+  if (hp && hr) { count_launch(); k_classify<true, true><<<grid, 128, 0, s>>>(P, first, count, outcome, length); }
+  else if (hp) { count_launch(); k_classify<true, false><<<grid, 128, 0, s>>>(P, first, count, outcome, length); }
+  else if (hr) { count_launch(); k_classify<false, true><<<grid, 128, 0, s>>>(P, first, count, outcome, length); }
+  else { count_launch(); k_classify<false, false><<<grid, 128, 0, s>>>(P, first, count, outcome, length); }
+  HSAW_CK(cudaGetLastError());
+  uint32_t h[2] = {0, 0};
+  HSAW_CK(cudaMemcpyAsync(h, d_ctr, 8, cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  dfree(d_ctr, s);
+  if (h[1] & ST_STEP_CAP) return fail(HSAW_E_STEP_CAP, "classify: a walk exceeded its step guard");
+  return HSAW_OK;
+}
+
+}  // namespace hsaw

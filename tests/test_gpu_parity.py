@@ -1,0 +1,325 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI (needs a GB300).
+
+Integer outputs (graph arrays, walk lists, histograms, greedy picks) must be bit-exact;
+FP64 estimates are formed from identical integer counts and must agree within 1e-12
+relative.  Sizes span many sampler chunks (256 attempts each) and a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tinygraphs import ONE, fx, random_tiny
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+hs = pytest.importorskip("paper_1702_05854_gb300")
+
+REL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+
+
+def both(n, src, dst, w):
+    return hs.hsaw_graph_from_edges(n, src, dst, w), oracle.Graph(n, src, dst, w)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    d = synth.workload_c1()
+    g, og = both(d["n"], d["src"], d["dst"], d["w"])
+    return d, g, og
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    d = synth.workload_rmat(14, "random", 50, 20, "node")
+    g, og = both(d["n"], d["src"], d["dst"], d["w"])
+    return d, g, og
+
+
+def assert_graph_equal(g, og):
+    a = g.export()
+    b = og.arrays()
+    for x, y, name in zip(a, b, ("row_ptr", "src", "dst", "thr", "input_index")):
+        assert np.array_equal(x, y), name
+
+
+# ----------------------------------------------------------------------------- a1 graph ingest
+def test_graph_ingest_matches_oracle(c1, rmat14):
+    assert_graph_equal(c1[1], c1[2])
+    assert_graph_equal(rmat14[1], rmat14[2])
+    for seed in range(5):
+        n, s, d, w = random_tiny(900 + seed, n=9, m=30)
+        assert_graph_equal(*both(n, s, d, w))
+
+
+def test_graph_ingest_edge_cases():
+    # one node, no edges
+    assert_graph_equal(*both(1, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32)))
+    # isolated nodes, self-loops, parallel edges, zero weights, full in-sum
+    src = np.array([0, 0, 2, 2, 3, 3, 3], np.int32)
+    dst = np.array([0, 1, 1, 1, 4, 4, 4], np.int32)
+    w = np.array([ONE, 7, 0, ONE - 7, 1, 2, 3], np.uint32)
+    assert_graph_equal(*both(6, src, dst, w))
+    # device-resident input arrays give the same graph
+    g = hs.hsaw_graph_from_edges(6, torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(),
+                                 torch.from_numpy(w.view(np.int32)).cuda())
+    assert_graph_equal(g, oracle.Graph(6, src, dst, w))
+
+
+def test_graph_ingest_errors():
+    src = np.array([0, 1], np.int32)
+    dst = np.array([2, 2], np.int32)
+    with pytest.raises(hs.HsawError) as e:
+        hs.hsaw_graph_from_edges(3, src, dst, np.array([0x80000000, 0x80000000], np.uint32))
+    assert e.value.status == -2
+    with pytest.raises(hs.HsawError) as e:
+        hs.hsaw_graph_from_edges(2, src, dst, np.array([1, 1], np.uint32))
+    assert e.value.status == -3
+    with pytest.raises(hs.HsawError) as e:
+        hs.hsaw_graph_from_csr(3, np.array([0, 2, 1, 2], np.int64), src, np.array([1, 1], np.uint32))
+    assert e.value.status == -1
+
+
+def test_graph_from_csr_matches(c1):
+    d, g, og = c1
+    rp, s, dd, thr, ii = og.arrays()
+    w = d["w"][ii]
+    g2 = hs.hsaw_graph_from_csr(d["n"], rp, s, w)
+    a = g2.export()
+    assert np.array_equal(a[0], rp) and np.array_equal(a[1], s) and np.array_equal(a[2], dd)
+    assert np.array_equal(a[3], thr) and np.array_equal(a[4], np.arange(d["m"]))
+
+
+# ----------------------------------------------------------------------------- a2/a3 walks
+def _q(d, **kw):
+    base = dict(sources=d["sources"], mode=hs.HSAW_EDGE if d["mode"] == "edge" else hs.HSAW_NODE, k=d["k"],
+                seed=synth.SEED_WALKS)
+    base.update(kw)
+    return hs.Query(**base)
+
+
+def _check_classify(g, og, q, first, count, oq):
+    out, ln = hs.hsaw_classify(g, q, first, count)
+    out, ln = out.cpu().numpy(), ln.cpu().numpy()
+    o2, l2 = oq.classify(first, count)
+    assert np.array_equal(out, o2)
+    nc = o2 != oracle.MISS_CYCLE
+    assert np.array_equal(ln[nc], l2[nc])
+    assert np.all(ln[~nc] >= l2[~nc])
+    return o2
+
+
+def test_classify_matches_oracle(c1, rmat14):
+    d, g, og = c1
+    o = _check_classify(g, og, _q(d), 0, 200_000, oracle.Query(og, d["sources"], seed=synth.SEED_WALKS))
+    assert (o == oracle.HIT).sum() > 100 and (o == oracle.MISS_CYCLE).sum() > 100
+    d, g, og = rmat14
+    _check_classify(g, og, _q(d), 10**9, 100_000, oracle.Query(og, d["sources"], seed=synth.SEED_WALKS))
+    # probabilistic suspects (NEXT-1 shape): coins on lane x1
+    d, g, og = c1
+    p = synth.probabilities(len(d["sources"]))
+    _check_classify(g, og, _q(d, p_fixed=p), 0, 100_000,
+                    oracle.Query(og, d["sources"], p_fixed=p, seed=synth.SEED_WALKS))
+
+
+def assert_stream_equal(walks, ostream):
+    aid, off, nodes, edges = walks.export()
+    W = ostream.export()
+    n = len(W)
+    assert np.array_equal(aid[:n], W.aid)
+    assert np.array_equal(off[:n + 1], W.node_off)
+    assert np.array_equal(nodes[:W.node_off[n]], W.nodes)
+    assert np.array_equal(edges[:W.node_off[n] - n], W.edges)
+
+
+@pytest.mark.parametrize("first", [0, 12345, (1 << 32) - 1000])
+def test_stream_matches_oracle_c1(c1, first):
+    d, g, og = c1
+    q = _q(d)
+    w = hs.hsaw_sample(g, q, first, 20_000)
+    assert w.info()["count"] >= 20_000
+    st = oracle.Stream(oracle.Query(og, d["sources"], seed=synth.SEED_WALKS), first_aid=first).extend(20_000)
+    assert_stream_equal(w, st)
+
+
+def test_stream_matches_oracle_variants(c1, rmat14):
+    d, g, og = rmat14
+    w = hs.hsaw_sample(g, _q(d), 0, 3000)
+    assert_stream_equal(w, oracle.Stream(oracle.Query(og, d["sources"], seed=synth.SEED_WALKS)).extend(3000))
+    d, g, og = c1
+    p = synth.probabilities(len(d["sources"]))
+    w = hs.hsaw_sample(g, _q(d, p_fixed=p, seed=99), 0, 5000)
+    assert_stream_equal(w, oracle.Stream(oracle.Query(og, d["sources"], p_fixed=p, seed=99)).extend(5000))
+
+
+def test_stream_residual_graph_matches_oracle():
+    for seed in range(4):
+        n, s, dd, w = random_tiny(700 + seed, n=8, m=20)
+        g, og = both(n, s, dd, w)
+        rng = np.random.default_rng(seed)
+        er = (rng.random(len(s)) < 0.2).astype(np.uint8)
+        nr = (rng.random(n) < 0.15).astype(np.uint8)
+        src = np.array([seed % n, (seed + 3) % n], np.int32)
+        q = hs.Query(sources=src, seed=seed + 1)
+        # removed masks are in CSR order for edges
+        rp, cs, cd, thr, ii = og.arrays()
+        walks = hs.hsaw_sample(g, q, 0, 2000, edge_removed=er, node_removed=nr)
+        ost = oracle.Stream(oracle.Query(og, src, edge_removed=er, node_removed=nr, seed=seed + 1)).extend(2000)
+        assert_stream_equal(walks, ost)
+
+
+# ----------------------------------------------------------------------------- a5/a6/a7 counting and greedy
+@pytest.fixture(scope="module")
+def c1_stream(c1):
+    d, g, og = c1
+    w = hs.hsaw_sample(g, _q(d), 0, 20_000)
+    st = oracle.Stream(oracle.Query(og, d["sources"], seed=synth.SEED_WALKS)).extend(20_000)
+    return d, g, og, w, st
+
+
+@pytest.mark.parametrize("mode", [hs.HSAW_EDGE, hs.HSAW_NODE])
+@pytest.mark.parametrize("rng_", [(0, 20_000), (1234, 7777), (19_999, 1)])
+def test_histogram_matches_oracle(c1_stream, mode, rng_):
+    d, g, og, w, st = c1_stream
+    first, count = rng_
+    M = d["m"] if mode == hs.HSAW_EDGE else d["n"]
+    uid, cnt = hs.hsaw_histogram(w, mode, first, count)
+    dense = st.histogram(mode, first, count, M)
+    nz = np.nonzero(dense)[0]
+    assert np.array_equal(uid, nz.astype(np.int32))
+    assert np.array_equal(cnt, dense[nz])
+
+
+@pytest.mark.parametrize("mode,k", [(hs.HSAW_EDGE, 10), (hs.HSAW_NODE, 50), (hs.HSAW_EDGE, 300)])
+def test_greedy_matches_oracle(c1_stream, mode, k):
+    d, g, og, w, st = c1_stream
+    M = d["m"] if mode == hs.HSAW_EDGE else d["n"]
+    ids, gains = hs.hsaw_greedy(w, g, mode, 0, 20_000, k)
+    oids, ogains = st.greedy(mode, 0, 20_000, M, k)
+    assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
+    # with a candidate mask (every third element)
+    cm = (np.arange(M) % 3 == 1).astype(np.uint8)
+    ids, gains = hs.hsaw_greedy(w, g, mode, 500, 9000, k, candidate_mask=cm)
+    oids, ogains = st.greedy(mode, 500, 9000, M, k, cand_mask=cm)
+    assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
+
+
+def test_greedy_zero_gain_fill():
+    # every walk is covered after one pick; the rest are zero-gain smallest-id candidates
+    n = 5
+    src = np.array([0, 1, 2], np.int32)
+    dst = np.array([1, 2, 3], np.int32)
+    w = np.array([ONE, ONE, ONE], np.uint32)
+    g, og = both(n, src, dst, w)
+    q = hs.Query(sources=np.array([0], np.int32), seed=3)
+    walks = hs.hsaw_sample(g, q, 0, 200)
+    st = oracle.Stream(oracle.Query(og, np.array([0], np.int32), seed=3)).extend(200)
+    for mode, M in ((hs.HSAW_NODE, n), (hs.HSAW_EDGE, 3)):
+        ids, gains = hs.hsaw_greedy(walks, g, mode, 0, 200, M)
+        oids, ogains = st.greedy(mode, 0, 200, M, M)
+        assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
+
+
+def test_coverage_matches_oracle(c1_stream):
+    d, g, og, w, st = c1_stream
+    rng = np.random.default_rng(5)
+    for mode, M in ((hs.HSAW_EDGE, d["m"]), (hs.HSAW_NODE, d["n"])):
+        for k in (1, 17, 400):
+            T = rng.choice(M, size=k, replace=False)
+            assert hs.hsaw_coverage(w, mode, 3000, 12_000, T) == st.coverage(mode, 3000, 12_000, M, T)
+
+
+# ----------------------------------------------------------------------------- full solves
+def assert_solve_equal(res_gpu, res_oracle):
+    ids, gains, r = res_gpu
+    oids, ogains, o = res_oracle
+    assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
+    for f in ("rounds_t", "hits", "attempts", "cov_R", "cov_Rprime", "hits_Rprime", "attempts_Rprime"):
+        assert r[f] == o[f], f
+    for f in ("spread_base_est", "spread_reduction_est", "eps_t"):
+        if math.isnan(o[f]):
+            assert math.isnan(r[f]), f
+        else:
+            assert r[f] == pytest.approx(o[f], rel=REL), f
+
+
+def test_solve_fixed_n_c1_full(c1):
+    """The eSI plain config: Chung-Lu 16,384 / 131,072, |S| = 16, k = 10, N = 200,000."""
+    d, g, og = c1
+    res = hs.hsaw_solve(g, _q(d, n_hsaw=d["n_hsaw"]))
+    ores = oracle.solve(oracle.Query(og, d["sources"], seed=synth.SEED_WALKS), oracle.MODE_EDGE, d["k"],
+                        n_hsaw=d["n_hsaw"])
+    assert_solve_equal(res, ores)
+
+
+def test_solve_stop_rule_matches_oracle(c1, rmat14):
+    d, g, og = c1
+    for mode, k in ((hs.HSAW_EDGE, 10), (hs.HSAW_NODE, 5)):
+        q = _q(d, mode=mode, k=k, sampling=hs.HSAW_STOP_RULE, eps=0.1)
+        res = hs.hsaw_solve(g, q)
+        ores = oracle.solve(oracle.Query(og, d["sources"], seed=synth.SEED_WALKS), mode, k, stop_rule=True,
+                            eps=0.1)
+        assert_solve_equal(res, ores)
+        assert res[2]["rounds_t"] >= 1
+    d, g, og = rmat14
+    q = _q(d, sampling=hs.HSAW_STOP_RULE, eps=0.2)
+    res = hs.hsaw_solve(g, q)
+    ores = oracle.solve(oracle.Query(og, d["sources"], seed=synth.SEED_WALKS), oracle.MODE_NODE, d["k"],
+                        stop_rule=True, eps=0.2)
+    assert_solve_equal(res, ores)
+
+
+def test_solve_with_candidates_and_probabilities(c1):
+    d, g, og = c1
+    p = synth.probabilities(len(d["sources"]))
+    cm = (np.arange(d["m"]) % 2 == 0).astype(np.uint8)
+    q = _q(d, n_hsaw=30_000, p_fixed=p, candidate_mask=cm, k=25)
+    res = hs.hsaw_solve(g, q)
+    ores = oracle.solve(oracle.Query(og, d["sources"], p_fixed=p, seed=synth.SEED_WALKS), oracle.MODE_EDGE, 25,
+                        n_hsaw=30_000, cand_mask=cm)
+    assert_solve_equal(res, ores)
+
+
+def test_solve_argument_errors(c1):
+    d, g, og = c1
+    bad = [dict(k=0), dict(k=d["m"] + 1), dict(sources=np.array([1, 1], np.int32)),
+           dict(sources=np.array([d["n"]], np.int32)), dict(sampling=hs.HSAW_STOP_RULE, eps=1.5),
+           dict(n_hsaw=0)]
+    for kw in bad:
+        base = dict(n_hsaw=100)
+        base.update(kw)
+        with pytest.raises(hs.HsawError):
+            hs.hsaw_solve(g, _q(d, **base))
+
+
+def test_solve_budget_timeout():
+    # the suspect is unreachable except by starting on it: a 1e-6 hit rate with a tiny budget
+    n = 1 << 16
+    g = hs.hsaw_graph_from_edges(n, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    with pytest.raises(hs.HsawError) as e:
+        hs.hsaw_solve(g, hs.Query(sources=np.array([5], np.int32), mode=hs.HSAW_NODE, k=1, n_hsaw=1000,
+                                     max_attempts=1 << 20))
+    assert e.value.status == -7
+
+
+def test_stop_constants_and_check_match_oracle():
+    for M, k, eps, delta in ((1 << 30, 1000, 0.1, 1 / (1 << 26)), (1 << 20, 100, 0.1, 1 / (1 << 20)),
+                             (131072, 10, 0.2, 1e-3)):
+        a = hs.hsaw_stop_constants(M, k, eps, delta)
+        b = oracle.stop_constants(M, k, eps, delta)
+        for key in a:
+            assert a[key] == pytest.approx(b[key], rel=1e-13), key
+    for c, cp, size, t in ((5000, 4000, 9000, 3), (3000, 3100, 4000, 1), (10, 10, 10, 1)):
+        ok1, e1 = hs.hsaw_check(c, cp, size, t, 0.1, 3137.84)
+        ok2, e2 = oracle.check(c, cp, size, t, 0.1, 3137.84)
+        assert ok1 == ok2 and (math.isnan(e1) and math.isnan(e2) or e1 == pytest.approx(e2, rel=1e-13))
