@@ -161,6 +161,29 @@ HSAW_API hsaw_status hsaw_walks_destroy(hsaw_walks w);
 HSAW_API hsaw_status hsaw_classify(hsaw_graph g, const hsaw_query* q, uint64_t first, int64_t count,
                           int8_t* outcome_dev, int32_t* length_dev, void* stream);
 
+/* ------------------------------------------------------------------ allocation-free sampling
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory: code running while a CUDA stream is being captured into a graph, or a
+ * host framework that owns every device allocation and forbids others.
+ *
+ * hsaw_sample_hits_static: the hits among attempts [first_attempt, first_attempt +
+ *   n_attempts) of graph g, in increasing attempt id: aid_out[i] (device, uint64) and
+ *   len_out[i] (device, uint32, nodes on the walk), *n_hits (host) = their number.  The
+ *   same hits, in the same order, as hsaw_sample over that range with p == 1 and no
+ *   removed elements.  suspect_bits: device array of ceil(n/32) words, bit v set iff v is
+ *   a source.  The call makes no device allocation: its scratch (about 2 MiB) is a
+ *   static array of the library that every GPU loading the library keeps until exit.
+ *   Errors: HSAW_E_INVALID for n_attempts outside [0, HSAW_STATIC_MAX_ATTEMPTS], NULL
+ *   arguments, or more hits than out_cap (then *n_hits is set and nothing is written).
+ *   The first call on a device looks up the scratch's device address (set-up); make it
+ *   before any stream capture.  Every call shares the one scratch array: calls that
+ *   overlap on the GPU (other threads or streams) race and must be serialised by the
+ *   caller.  The call synchronises `stream` before it returns. */
+#define HSAW_STATIC_MAX_ATTEMPTS (1u << 18)
+HSAW_API hsaw_status hsaw_sample_hits_static(hsaw_graph g, const uint32_t* suspect_bits, uint64_t seed,
+                                             uint64_t first_attempt, int64_t n_attempts, uint64_t* aid_out,
+                                             uint32_t* len_out, int64_t out_cap, int64_t* n_hits, void* stream);
+
 /* ------------------------------------------------------------------ counting and greedy
  * Over walks [first, first + count) of a stream, in mode (edges: R_j = the walk's edges;
  * nodes: R_j = all of v_1..v_l, start and hit source included).

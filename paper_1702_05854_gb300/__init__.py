@@ -70,6 +70,7 @@ SIGNATURES = {
     "hsaw_coverage": (ctypes.c_int, [_p, ctypes.c_int, _i64, _i64, _p, _i32, ctypes.POINTER(_u64), _p]),
     "hsaw_stop_constants": (ctypes.c_int, [_i64, _i32, _dbl, _dbl, _p]),
     "hsaw_check": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, _dbl, _dbl, ctypes.POINTER(_dbl)]),
+    "hsaw_sample_hits_static": (ctypes.c_int, [_p, _p, _u64, _u64, _i64, _p, _p, _i64, ctypes.POINTER(_i64), _p]),
     "hsaw_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "hsaw_profile_read": (ctypes.c_int, [ctypes.POINTER(hsaw_profile)]),
     "hsaw_last_error": (ctypes.c_char_p, []),
@@ -287,6 +288,22 @@ def hsaw_sample(graph: Graph, query: Query, first_attempt: int, n_hits: int, edg
     _check(load().hsaw_sample(graph.handle, ctypes.byref(q), first_attempt, n_hits, _ptr(er), _ptr(nr), 0,
                               ctypes.byref(h), _stream(stream)))
     return Walks(h)
+
+
+HSAW_STATIC_MAX_ATTEMPTS = 1 << 18
+
+
+def hsaw_sample_hits_static(graph: Graph, suspect_bits, seed: int, first_attempt: int, n_attempts: int, aid_out,
+                            len_out, stream=None) -> int:
+    """Allocation-free hit search over an attempt range (see include/hsaw.h).
+
+    suspect_bits, aid_out (int64 view of uint64) and len_out (int32 view of uint32) are
+    caller-owned torch CUDA tensors; returns the number of hits written."""
+    n = _i64()
+    _check(load().hsaw_sample_hits_static(graph.handle, _ptr(suspect_bits), seed, first_attempt, n_attempts,
+                                          _ptr(aid_out), _ptr(len_out), int(aid_out.numel()), ctypes.byref(n),
+                                          _stream(stream)))
+    return int(n.value)
 
 
 def hsaw_classify(graph: Graph, query: Query, first: int, count: int, stream=None):

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "solver.cuh"
@@ -455,3 +456,142 @@ hsaw_status classify_attempts(const Graph& g, const QueryDev& qd, uint64_t first
 }
 
 }  // namespace hsaw
+
+// ------------------------------------------------------------------ allocation-free variant
+// Scratch of hsaw_sample_hits_static: file-scope device arrays sized for at most
+// HSAW_STATIC_MAX_ATTEMPTS attempts per call (about 2 MiB in total).  Every GPU that loads
+// this library holds them until the process exits.  Host code cannot pass these names to
+// a kernel (in host code they are stand-ins, not device addresses); their device
+// addresses are looked up once per device with cudaGetSymbolAddress.
+namespace hsaw {
+
+constexpr uint32_t STATIC_CHUNK = 256;
+constexpr uint32_t STATIC_CHUNKS = HSAW_STATIC_MAX_ATTEMPTS / STATIC_CHUNK;
+
+static __device__ __align__(256) uint32_t g_static_ctrs[8];                 // work counter, status, total
+static __device__ __align__(256) unsigned long long g_static_steps[1];
+static __device__ __align__(256) uint32_t g_static_chunk_hits[STATIC_CHUNKS];
+static __device__ __align__(256) uint32_t g_static_chunk_off[STATIC_CHUNKS];
+static __device__ __align__(256) uint2 g_static_recs[STATIC_CHUNKS * STATIC_CHUNK];
+
+struct StaticScratch {
+  uint32_t* ctrs = nullptr;
+  unsigned long long* steps = nullptr;
+  uint32_t* chunk_hits = nullptr;
+  uint32_t* chunk_off = nullptr;
+  uint2* recs = nullptr;
+  bool ready = false;
+};
+static StaticScratch g_static_dev[64];
+static std::mutex g_static_mu;
+
+// Device addresses of the static scratch on the current device (set-up on first use).
+static hsaw_status static_scratch(StaticScratch** out) {
+  int dev = 0;
+  HSAW_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(HSAW_E_DEVICE, "static sampler: device index out of range");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticScratch& s = g_static_dev[dev];
+  if (!s.ready) {
+    HSAW_CK(cudaGetSymbolAddress((void**)&s.ctrs, g_static_ctrs));
+    HSAW_CK(cudaGetSymbolAddress((void**)&s.steps, g_static_steps));
+    HSAW_CK(cudaGetSymbolAddress((void**)&s.chunk_hits, g_static_chunk_hits));
+    HSAW_CK(cudaGetSymbolAddress((void**)&s.chunk_off, g_static_chunk_off));
+    HSAW_CK(cudaGetSymbolAddress((void**)&s.recs, g_static_recs));
+    s.ready = true;
+  }
+  *out = &s;
+  return HSAW_OK;
+}
+
+// Single-block exclusive scan of at most STATIC_CHUNKS counts (clamped to cap); writes the
+// total to *total.  One block of 1024 threads, no temporary memory.
+__global__ void __launch_bounds__(1024) k_static_scan(const uint32_t* __restrict__ in, uint32_t n, uint32_t cap,
+                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ total) {
+  __shared__ uint32_t warp_sum[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < n ? min(in[i], cap) : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[w] = x;
+    __syncthreads();
+    uint32_t before = carry;
+    for (int k = 0; k < w; ++k) before += warp_sum[k];
+    if (i < n) out[i] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+}  // namespace hsaw
+
+extern "C" hsaw_status hsaw_sample_hits_static(hsaw_graph g, const uint32_t* suspect_bits, uint64_t seed,
+                                               uint64_t first_attempt, int64_t n_attempts, uint64_t* aid_out,
+                                               uint32_t* len_out, int64_t out_cap, int64_t* n_hits, void* stream) {
+  using namespace hsaw;
+  if (!g || !suspect_bits || !n_hits || (out_cap > 0 && (!aid_out || !len_out)))
+    return fail(HSAW_E_INVALID, "static sampler: NULL argument");
+  *n_hits = 0;
+  if (n_attempts < 0 || n_attempts > (int64_t)HSAW_STATIC_MAX_ATTEMPTS)
+    return fail(HSAW_E_INVALID, "static sampler: n_attempts must be in [0, HSAW_STATIC_MAX_ATTEMPTS]");
+  if (n_attempts == 0) return HSAW_OK;
+  StaticScratch* sc = nullptr;
+  HSAW_TRY(static_scratch(&sc));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Graph& G = g->g;
+  SampleParams P{};
+  P.node = G.node;
+  P.edge = G.edge;
+  P.s_bits = suspect_bits;
+  P.n = (uint32_t)G.n;
+  P.k0 = (uint32_t)seed;
+  P.k1 = (uint32_t)(seed >> 32);
+  P.step_cap = (uint32_t)std::min<uint64_t>(4ull * (uint64_t)G.n + 64ull, 0xFFFFFFF0ull);
+  const uint32_t n_chunks = (uint32_t)((n_attempts + STATIC_CHUNK - 1) / STATIC_CHUNK);
+  P.a0 = first_attempt;
+  P.n_attempts = (uint32_t)n_attempts;
+  P.chunk = STATIC_CHUNK;
+  P.n_chunks = n_chunks;
+  P.cap = STATIC_CHUNK;  // room for every attempt of a chunk to hit: no overflow
+  P.chunk_ctr = sc->ctrs;
+  P.chunk_hits = sc->chunk_hits;
+  P.recs = sc->recs;
+  P.steps = sc->steps;
+  // the shared scratch keeps the previous call's contents: clear what must start at zero
+  HSAW_CK(cudaMemsetAsync(sc->ctrs, 0, sizeof(g_static_ctrs), s));
+  HSAW_CK(cudaMemsetAsync(sc->steps, 0, sizeof(g_static_steps), s));
+  HSAW_CK(cudaMemsetAsync(sc->chunk_hits, 0, (size_t)n_chunks * sizeof(uint32_t), s));
+  const unsigned grid = (unsigned)std::max(1, std::min<int>(sm_count() * sample_blocks_per_sm(),
+                                                             (int)((n_chunks + 7) / 8)));
+  count_launch();
+  k_sample<false, false><<<grid, 256, 0, s>>>(P);
+  HSAW_CK(cudaGetLastError());
+  count_launch();
+  k_static_scan<<<1, 1024, 0, s>>>(sc->chunk_hits, n_chunks, STATIC_CHUNK, sc->chunk_off, sc->ctrs + 2);
+  HSAW_CK(cudaGetLastError());
+  uint32_t h[4] = {0, 0, 0, 0};
+  HSAW_CK(cudaMemcpyAsync(h, sc->ctrs, sizeof(h), cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  if (h[1] & ST_STEP_CAP) return fail(HSAW_E_STEP_CAP, "static sampler: a walk exceeded its step guard");
+  *n_hits = h[2];
+  if ((int64_t)h[2] > out_cap) return fail(HSAW_E_INVALID, "static sampler: more hits than out_cap");
+  if (h[2]) {
+    count_launch();
+    k_compact<<<grid_for((size_t)n_chunks * 32, 256, 8192), 256, 0, s>>>(
+        sc->chunk_hits, sc->chunk_off, sc->recs, STATIC_CHUNK, n_chunks, first_attempt, aid_out, len_out);
+    HSAW_CK(cudaGetLastError());
+  }
+  HSAW_CK(cudaStreamSynchronize(s));
+  return HSAW_OK;
+}
