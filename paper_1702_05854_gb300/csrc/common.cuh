@@ -62,10 +62,16 @@ struct DBuf {  // grow-only device buffer
 // (0 if the in-weights differ), in-sum}; edge[e] = {tail node u of (u, v), running sum of
 // v's in-weights through e}.  In-edge j of v is live for a draw r iff
 // thr[j-1] <= r < thr[j]; none is live when r >= in-sum.
+// erec[2e], erec[2e+1] = the 32-byte walk record of edge e = (u, v): {u, node[u].x,
+// node[u].y, node[u].z}, {node[u].w, thr[e], 0, 0}.  One sector read gives both the tail
+// node and everything the next draw at u needs, so a walk makes one dependent DRAM access
+// per live-edge draw at equal-weight nodes (the tail's record is replicated per in-edge:
+// 32 B per edge of HBM for half the dependent latency and DRAM sectors per draw).
 struct Graph {
   int64_t n = 0, m = 0;
   uint4* node = nullptr;
   uint2* edge = nullptr;
+  uint4* erec = nullptr;
   int64_t* input_index = nullptr;  // CSR position -> input edge index (NULL = identity)
   int device = 0;
 };

@@ -151,6 +151,17 @@ __global__ void k_thresholds(const uint32_t* __restrict__ row_start, int64_t n, 
   }
 }
 
+// 32-byte walk records (see Graph::erec).
+__global__ void k_walk_records(const uint2* __restrict__ edge, const uint4* __restrict__ node, int64_t m,
+                               uint4* __restrict__ erec) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 ed = edge[e];
+    const uint4 nu = node[ed.x];
+    erec[2 * e] = make_uint4(ed.x, nu.x, nu.y, nu.z);
+    erec[2 * e + 1] = make_uint4(nu.w, ed.y, 0u, 0u);
+  }
+}
+
 // ------------------------------------------------------------------ host
 static hsaw_status check_err(uint32_t* d_err, cudaStream_t s) {
   uint32_t h = 0;
@@ -179,6 +190,8 @@ static void destroy_graph(Graph& g) {
   if (g.node) cudaFree(g.node);
   if (g.edge) cudaFree(g.edge);
   if (g.input_index) cudaFree(g.input_index);
+  if (g.erec) cudaFree(g.erec);
+  g.erec = nullptr;
   g.node = nullptr;
   g.edge = nullptr;
   g.input_index = nullptr;
@@ -190,6 +203,7 @@ static hsaw_status alloc_graph(Graph& g, int64_t n, int64_t m, bool with_index) 
   cudaGetDevice(&g.device);
   HSAW_CK(cudaMalloc((void**)&g.node, (size_t)n * sizeof(uint4)));
   HSAW_CK(cudaMalloc((void**)&g.edge, (size_t)(m ? m : 1) * sizeof(uint2)));
+  HSAW_CK(cudaMalloc((void**)&g.erec, (size_t)(m ? m : 1) * 2 * sizeof(uint4)));
   if (with_index) HSAW_CK(cudaMalloc((void**)&g.input_index, (size_t)(m ? m : 1) * sizeof(int64_t)));
   return HSAW_OK;
 }
@@ -215,7 +229,13 @@ static hsaw_status finish_graph(Graph& g, uint32_t* row_start, uint32_t* d_err, 
   count_launch();
   k_thresholds<<<grid_for((size_t)n * 32, 256, 1u << 20), 256, 0, s>>>(row_start, n, g.edge, g.node, d_err);
   HSAW_CK(cudaGetLastError());
-  return check_err(d_err, s);
+  HSAW_TRY(check_err(d_err, s));
+  if (g.m) {
+    count_launch();
+    k_walk_records<<<grid_for(g.m, 256, 1u << 16), 256, 0, s>>>(g.edge, g.node, g.m, g.erec);
+    HSAW_CK(cudaGetLastError());
+  }
+  return HSAW_OK;
 }
 
 static hsaw_status from_edges(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const uint32_t* w,

@@ -26,6 +26,7 @@ enum : uint32_t { ST_OVERFLOW = 1u, ST_STEP_CAP = 2u };
 struct SampleParams {
   const uint4* __restrict__ node;
   const uint2* __restrict__ edge;
+  const uint4* __restrict__ erec;
   const uint32_t* __restrict__ s_bits;
   const uint32_t* __restrict__ p32;
   const uint8_t* __restrict__ edge_removed;
@@ -44,15 +45,45 @@ struct SampleParams {
   unsigned long long* steps;
 };
 
+// Exact cycle detection in registers: the walk keeps the nodes it saw at positions
+// 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 18, ... (each 1.25x the last) in a ring of 8
+// registers.  A tail node equal to a kept node is a revisit, so the world's backward chain
+// is a cycle (miss); a cycle entered at position mu is seen within about 0.25 mu + lambda
+// draws, against mu + lambda for a whole-walk check and about 2 (mu + lambda) for Brent.
+struct Ckpt {
+  uint32_t c0, c1, c2, c3, c4, c5, c6, c7;
+  uint32_t count, next;
+  __device__ __forceinline__ void reset(uint32_t v) {
+    c0 = c1 = c2 = c3 = c4 = c5 = c6 = c7 = v;
+    count = 1;
+    next = 1;
+  }
+  __device__ __forceinline__ bool seen(uint32_t u) const {
+    return (u == c0) | (u == c1) | (u == c2) | (u == c3) | (u == c4) | (u == c5) | (u == c6) | (u == c7);
+  }
+  // u is the node at walk position pos (>= 1)
+  __device__ __forceinline__ void keep(uint32_t u, uint32_t pos) {
+    if (pos < next) return;
+    const uint32_t slot = count & 7u;
+    c0 = slot == 0 ? u : c0; c1 = slot == 1 ? u : c1; c2 = slot == 2 ? u : c2; c3 = slot == 3 ? u : c3;
+    c4 = slot == 4 ? u : c4; c5 = slot == 5 ? u : c5; c6 = slot == 6 ? u : c6; c7 = slot == 7 ? u : c7;
+    ++count;
+    next = next + max(1u, next >> 2);
+  }
+};
+
 template <bool HAS_P, bool HAS_REM>
-__global__ void __launch_bounds__(256) k_sample(SampleParams P) {
+__global__ void __launch_bounds__(256, 6) k_sample(SampleParams P) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   uint32_t cur = 0, cur_end = 0;  // warp's attempt cursor within the launch
   bool more = true;
   bool active = false;
-  uint32_t off = 0, v = 0, tort = 0, power = 1, lam = 0, len = 0;
+  uint32_t off = 0, v = 0, len = 0;
+  uint4 rec = make_uint4(0, 0, 0, 0);  // node record of v: first in-edge, in-degree, equal weight, in-sum
+  Ckpt ck;
+  ck.reset(0);
   unsigned long long my_steps = 0;
   for (;;) {
     unsigned need = __ballot_sync(FULL, !active);
@@ -70,11 +101,9 @@ __global__ void __launch_bounds__(256) k_sample(SampleParams P) {
       const uint32_t rank = __popc(need & lt);
       if (!active && rank < avail) {
         off = cur + rank;
-        const uint64_t a = P.a0 + off;
-        v = start_node(a, P.n, P.k0, P.k1);
-        tort = v;
-        power = 1;
-        lam = 0;
+        v = start_node(P.a0 + off, P.n, P.k0, P.k1);
+        rec = __ldg(&P.node[v]);
+        ck.reset(v);
         len = 1;
         active = true;
       }
@@ -83,36 +112,38 @@ __global__ void __launch_bounds__(256) k_sample(SampleParams P) {
     }
     if (!__any_sync(FULL, active)) break;
     if (active) {
-      // one step of the walk at node v (Alg. 1 lines 5-13)
+      // one live-edge draw at node v (Alg. 1 lines 5-13); the tail's record comes with it
       const uint64_t a = P.a0 + off;
       int outcome = -1;  // -1 continue, 0 miss, 1 hit
       if (HAS_REM && len == 1 && P.node_removed && P.node_removed[v]) outcome = 0;
       if (outcome < 0) {
         const uint32_t sw = __ldg(&P.s_bits[v >> 5]);
-        const uint4 nd = __ldg(&P.node[v]);
+        const uint4 x = node_draw(a, v, P.k0, P.k1);
+        const bool live = x.x < rec.w;
+        uint4 ra = make_uint4(0, 0, 0, 0), rb = make_uint4(0, 0, 0, 0);
+        uint32_t e = 0;
+        if (live) {
+          e = rec.x + pick_in_edge(P.edge, rec, x.x);
+          ra = __ldg(&P.erec[2 * (size_t)e]);
+          rb = __ldg(&P.erec[2 * (size_t)e + 1]);
+        }
         const bool suspect = (sw >> (v & 31)) & 1u;
-        if (!HAS_P && suspect) {
+        if (suspect && (!HAS_P || source_coin(x.y, __ldg(&P.p32[v])))) {
           outcome = 1;
         } else {
-          const uint4 x = node_draw(a, v, P.k0, P.k1);
-          if (HAS_P && suspect && source_coin(x.y, __ldg(&P.p32[v]))) {
-            outcome = 1;
-          } else if (++my_steps, x.x >= nd.w) {
+          ++my_steps;
+          if (!live) {
             outcome = 0;  // no live in-edge
           } else {
-            const uint32_t e = nd.x + pick_in_edge(P.edge, nd, x.x);
-            const uint32_t u = __ldg(&P.edge[e].x);
+            const uint32_t u = ra.x;
             if (HAS_REM && ((P.edge_removed && P.edge_removed[e]) || (P.node_removed && P.node_removed[u]))) {
               outcome = 0;
-            } else if (u == tort) {
-              outcome = 0;  // Brent: the walk closed a cycle
+            } else if (ck.seen(u)) {
+              outcome = 0;  // the walk closed a cycle
             } else {
-              if (++lam == power) {
-                tort = u;
-                power <<= 1;
-                lam = 0;
-              }
+              ck.keep(u, len);
               v = u;
+              rec = make_uint4(ra.y, ra.z, ra.w, rb.x);
               if (++len > P.step_cap) {
                 atomicOr(P.chunk_ctr + 1, ST_STEP_CAP);
                 outcome = 0;
@@ -124,9 +155,9 @@ __global__ void __launch_bounds__(256) k_sample(SampleParams P) {
       if (outcome >= 0) {
         active = false;
         if (outcome == 1) {
-          const uint32_t ck = off / P.chunk;
-          const uint32_t slot = atomicAdd(&P.chunk_hits[ck], 1u);
-          if (slot < P.cap) P.recs[(size_t)ck * P.cap + slot] = make_uint2(off, len);
+          const uint32_t ck_i = off / P.chunk;
+          const uint32_t slot = atomicAdd(&P.chunk_hits[ck_i], 1u);
+          if (slot < P.cap) P.recs[(size_t)ck_i * P.cap + slot] = make_uint2(off, len);
           else atomicOr(P.chunk_ctr + 1, ST_OVERFLOW);
         }
       }
@@ -302,6 +333,7 @@ static SampleParams make_params(const Graph& g, const QueryDev& qd) {
   SampleParams P{};
   P.node = g.node;
   P.edge = g.edge;
+  P.erec = g.erec;
   P.s_bits = qd.s_bits;
   P.p32 = qd.p32;
   P.edge_removed = qd.edge_removed;
@@ -553,6 +585,7 @@ extern "C" hsaw_status hsaw_sample_hits_static(hsaw_graph g, const uint32_t* sus
   SampleParams P{};
   P.node = G.node;
   P.edge = G.edge;
+  P.erec = G.erec;
   P.s_bits = suspect_bits;
   P.n = (uint32_t)G.n;
   P.k0 = (uint32_t)seed;
