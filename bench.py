@@ -166,7 +166,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-attempts", type=int, default=400_000)
+    ap.add_argument("--ref-attempts", type=int, default=50_000)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -244,7 +244,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_sample", "peak_source": "measured" if peaks else "fallback",
                 "sampler_share_of_step": prof["sampler_ms"] / 1e3 / elapsed,
-                "steps_per_s": prof["sampler_steps"] / (prof["sampler_ms"] / 1e3) if prof["sampler_ms"] else 0.0}
+                "steps_per_s": prof["sampler_steps"] / (prof["sampler_ms"] / 1e3) if prof["sampler_ms"] else 0.0,
+                "phase_ms_per_step": {k_: v_ / args.steps for k_, v_ in prof["phase_ms"].items()}}
 
     # end to end through the C ABI with host buffers: graph ingest from host arrays + solve
     e2e = None

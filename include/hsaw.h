@@ -219,6 +219,8 @@ typedef struct {
   double sampler_ms;          /* summed device time of the timed sampler launches */
   uint64_t sampler_steps;     /* live-edge draws executed by those launches */
   uint64_t sampler_attempts;  /* attempts examined by those launches */
+  double phase_ms[8];         /* device time per phase: 0 sampling (launch, compaction, re-walk),
+                                 1 counting + inverted index, 2 greedy, 3 out-of-sample coverage */
 } hsaw_profile;
 HSAW_API hsaw_status hsaw_profile_enable(int on);
 HSAW_API hsaw_status hsaw_profile_read(hsaw_profile* out);

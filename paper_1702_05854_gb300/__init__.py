@@ -48,7 +48,7 @@ class hsaw_result(ctypes.Structure):
 
 class hsaw_profile(ctypes.Structure):
     _fields_ = [("kernel_launches", _u64), ("sampler_launches", _u64), ("sampler_ms", _dbl),
-                ("sampler_steps", _u64), ("sampler_attempts", _u64)]
+                ("sampler_steps", _u64), ("sampler_attempts", _u64), ("phase_ms", _dbl * 8)]
 
 
 # name -> (restype, argtypes); mirrors include/hsaw.h
@@ -352,7 +352,10 @@ def hsaw_profile_enable(on: bool = True):
 def hsaw_profile_read():
     p = hsaw_profile()
     _check(load().hsaw_profile_read(ctypes.byref(p)))
-    return {f: getattr(p, f) for f, _ in hsaw_profile._fields_}
+    d = {f: getattr(p, f) for f, _ in hsaw_profile._fields_ if f != "phase_ms"}
+    d["phase_ms"] = {"sampling": p.phase_ms[0], "counting": p.phase_ms[1], "greedy": p.phase_ms[2],
+                     "coverage": p.phase_ms[3]}
+    return d
 
 
 def hsaw_last_error() -> str:

@@ -106,9 +106,15 @@ static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cu
   r->eps_t = NAN;
   if (q->sampling == HSAW_FIXED_N) {
     if (q->n_hsaw < 1) return fail(HSAW_E_INVALID, "query: n_hsaw < 1");
+    void* ph = phase_begin(s);
     HSAW_TRY(stream_extend(g, W.qd, W.st, q->n_hsaw, s));
+    phase_end(ph, s, PH_SAMPLE);
+    ph = phase_begin(s);
     HSAW_TRY(cover_build(W.st, q->mode, 0, q->n_hsaw, W.cv, s));
+    phase_end(ph, s, PH_COUNT);
+    ph = phase_begin(s);
     HSAW_TRY(cover_greedy(W.cv, W.cand, M, k, r->ids, r->gains, s));
+    phase_end(ph, s, PH_GREEDY);
     uint64_t last = 0;
     HSAW_TRY(aid_at(W.st, q->n_hsaw - 1, &last, s));
     uint64_t cov = 0;
@@ -130,13 +136,21 @@ static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cu
     for (int32_t t = 1;; ++t) {
       if (t > 40 || (L << (t - 1)) > (int64_t)1 << 30) return fail(HSAW_E_NOMEM, "stop rule: sample budget beyond device limits");
       const int64_t half = L << (t - 1);
+      void* ph = phase_begin(s);
       HSAW_TRY(stream_extend(g, W.qd, W.st, 2 * half, s));
+      phase_end(ph, s, PH_SAMPLE);
+      ph = phase_begin(s);
       HSAW_TRY(cover_build(W.st, q->mode, 0, half, W.cv, s));
+      phase_end(ph, s, PH_COUNT);
+      ph = phase_begin(s);
       HSAW_TRY(cover_greedy(W.cv, W.cand, M, k, ids.data(), gains.data(), s));
+      phase_end(ph, s, PH_GREEDY);
       uint64_t cov = 0;
       for (int32_t i = 0; i < k; ++i) cov += gains[i];
       uint64_t covp = 0;
+      ph = phase_begin(s);
       HSAW_TRY(cover_count(W.st, q->mode, half, half, ids.data(), k, &covp, s));
+      phase_end(ph, s, PH_COVERAGE);
       double et;
       const int ok = check_bound((double)cov, (double)covp, (double)half, t, q->eps, lam1, &et);
       uint64_t a_half = 0, a_all = 0;

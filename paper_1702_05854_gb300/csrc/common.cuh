@@ -140,6 +140,10 @@ void count_launch();
 void* profile_begin(cudaStream_t s);
 void profile_end(void* token, cudaStream_t s, uint64_t attempts);
 void profile_add_steps(uint64_t steps);
+// Phase timing (profiling only): 0 sampling, 1 counting + index, 2 greedy, 3 coverage.
+enum { PH_SAMPLE = 0, PH_COUNT = 1, PH_GREEDY = 2, PH_COVERAGE = 3 };
+void* phase_begin(cudaStream_t s);
+void phase_end(void* token, cudaStream_t s, int phase);
 
 }  // namespace hsaw
 

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "solver.cuh"
@@ -22,7 +23,7 @@ enum : uint32_t { GS_BARRIER_TIMEOUT = 1u };
 void Cover::release(cudaStream_t s) {
   keys.release(s); vals.release(s); keys2.release(s); vals2.release(s); run_flag.release(s);
   uid.release(s); cnt.release(s); inv_off.release(s); inv_walk.release(s); entry_uidx.release(s);
-  walk_eoff.release(s); cnt_work.release(s); covered.release(s); allowed.release(s); partial.release(s);
+  walk_eoff.release(s); cnt_work.release(s); covered.release(s); dirty.release(s); partial.release(s);
   misc.release(s);
 }
 
@@ -142,16 +143,25 @@ hsaw_status cover_build(const Stream& st, hsaw_mode mode, int64_t first, int64_t
 }
 
 // ------------------------------------------------------------------ greedy
+// Running counts carry an exclusion flag in bit 31 (not a candidate, or already picked).
+// The argmax key of element u is (count << 32) | (2^32 - 1 - u): the largest count wins and
+// ties go to the smallest index, i.e. the smallest id (ids increase with u).  Elements are
+// grouped by 256; each group caches its largest key and is refreshed only when one of its
+// counts changed (dirty flag), and each CTA owns a fixed range of groups.
+constexpr uint32_t GREEDY_GROUP = 256;
+constexpr uint32_t EXCLUDED = 0x80000000u;
+
 struct GreedyParams {
-  uint32_t U;
+  uint32_t U, NG;
   int32_t k;
-  uint32_t* cnt;  // running marginal counts
+  uint32_t* cnt;  // running marginal counts | EXCLUDED
   const uint32_t* inv_off;
   const uint32_t* inv_walk;
   const uint32_t* walk_eoff;
   const uint32_t* entry_uidx;
   uint8_t* covered;
-  uint8_t* allowed;
+  unsigned long long* gkey;  // NG: cached largest key of each group
+  uint8_t* dirty;            // NG
   unsigned long long* partial;  // gridDim.x
   uint32_t* out_u;
   uint32_t* out_gain;
@@ -174,8 +184,8 @@ __device__ __forceinline__ void grid_barrier(uint32_t* ctl, unsigned nblocks) {
       } else {
         uint32_t spins = 0;
         while (*vgen == g) {
-          __nanosleep(100);
-          if (++spins > (1u << 24)) {  // ~2 s: record and stop waiting
+          __nanosleep(32);
+          if (++spins > (1u << 26)) {  // a few seconds: record and stop waiting
             atomicOr(ctl + 2, GS_BARRIER_TIMEOUT);
             break;
           }
@@ -188,43 +198,68 @@ __device__ __forceinline__ void grid_barrier(uint32_t* ctl, unsigned nblocks) {
   __syncthreads();
 }
 
-__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sm) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    unsigned long long y = __shfl_down_sync(0xffffffffu, v, o);
+    unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
     v = y > v ? y : v;
   }
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_max_u64(v);
   __syncthreads();
   if (lane == 0) sm[w] = v;
   __syncthreads();
   if (w == 0) {
     v = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ull;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      unsigned long long y = __shfl_down_sync(0xffffffffu, v, o);
-      v = y > v ? y : v;
-    }
+    v = warp_max_u64(v);
     if (lane == 0) sm[32] = v;
   }
   __syncthreads();
   return sm[32];
 }
 
+__device__ __forceinline__ unsigned long long elem_key(uint32_t c, uint32_t u) {
+  return ((c & EXCLUDED) || c == 0) ? 0ull : (((unsigned long long)c << 32) | (0xFFFFFFFFu - u));
+}
+
 __global__ void __launch_bounds__(512) k_greedy(GreedyParams P) {
   __shared__ unsigned long long sm[33];
   const unsigned G = gridDim.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t gsz = (size_t)G * blockDim.x;
+  const uint32_t g0 = (uint32_t)((uint64_t)P.NG * blockIdx.x / G);
+  const uint32_t g1 = (uint32_t)((uint64_t)P.NG * (blockIdx.x + 1) / G);
   int32_t r = 0;
   for (; r < P.k; ++r) {
-    unsigned long long best = 0;
-    for (size_t u = gtid; u < P.U; u += gsz) {
-      // counts, flags and partials change across blocks between barriers: read them from L2
-      if (__ldcg(&P.allowed[u])) {
-        const unsigned long long key = ((unsigned long long)__ldcg(&P.cnt[u]) << 32) | (0xFFFFFFFFu - (uint32_t)u);
-        best = key > best ? key : best;
+    // refresh this CTA's dirty groups (one warp per group)
+    for (uint32_t g = g0 + w; g < g1; g += nw) {
+      if (__ldcg(&P.dirty[g])) {
+        unsigned long long best = 0;
+        const uint32_t base = g * GREEDY_GROUP;
+        for (uint32_t i = lane; i < GREEDY_GROUP; i += 32) {
+          const uint32_t u = base + i;
+          if (u < P.U) {
+            const unsigned long long key = elem_key(__ldcg(&P.cnt[u]), u);
+            best = key > best ? key : best;
+          }
+        }
+        best = warp_max_u64(best);
+        if (lane == 0) {
+          P.gkey[g] = best;
+          P.dirty[g] = 0;
+        }
       }
+    }
+    __syncthreads();
+    unsigned long long best = 0;
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+      const unsigned long long x = P.gkey[g];
+      best = x > best ? x : best;
     }
     best = block_max_u64(best, sm);
     if (threadIdx.x == 0) P.partial[blockIdx.x] = best;
@@ -241,14 +276,20 @@ __global__ void __launch_bounds__(512) k_greedy(GreedyParams P) {
     if (gtid == 0) {
       P.out_u[r] = u;
       P.out_gain[r] = gain;
-      P.allowed[u] = 0;
+      atomicOr(&P.cnt[u], EXCLUDED);
+      P.dirty[u / GREEDY_GROUP] = 1;
     }
+    // mark the picked element's uncovered walks and take their elements' counts down
     const uint32_t q0 = P.inv_off[u], q1 = P.inv_off[u + 1];
     for (size_t q = q0 + gtid; q < q1; q += gsz) {
       const uint32_t j = P.inv_walk[q];
       if (!__ldcg(&P.covered[j])) {
         P.covered[j] = 1;
-        for (uint32_t p = P.walk_eoff[j]; p < P.walk_eoff[j + 1]; ++p) atomicSub(&P.cnt[P.entry_uidx[p]], 1u);
+        for (uint32_t p = P.walk_eoff[j]; p < P.walk_eoff[j + 1]; ++p) {
+          const uint32_t x = P.entry_uidx[p];
+          atomicSub(&P.cnt[x], 1u);
+          P.dirty[x / GREEDY_GROUP] = 1;
+        }
       }
     }
     grid_barrier(P.ctl, G);
@@ -256,10 +297,123 @@ __global__ void __launch_bounds__(512) k_greedy(GreedyParams P) {
   if (gtid == 0) P.ctl[3] = (uint32_t)r;
 }
 
-__global__ void k_allowed(const int32_t* __restrict__ uid, uint32_t U, const uint8_t* __restrict__ cand,
-                          uint8_t* __restrict__ allowed) {
+// ------------------------------------------------------------------ greedy on one cluster
+// The same greedy on one thread-block cluster: the per-group largest counts live in the
+// CTAs' shared memory (CTA r owns groups [r * per_cta, (r + 1) * per_cta)), decrements
+// mark the owner's dirty bit with an atomic on its shared memory (distributed shared
+// memory), and phases are separated by the hardware cluster barrier instead of a barrier
+// on global memory.  Group g covers elements [g << gshift, (g + 1) << gshift).
+namespace cg = cooperative_groups;
+
+struct ClusterGreedyParams {
+  uint32_t U, NG, per_cta, gshift;
+  int32_t k;
+  uint32_t* cnt;  // running counts | EXCLUDED
+  const uint32_t* inv_off;
+  const uint32_t* inv_walk;
+  const uint32_t* walk_eoff;
+  const uint32_t* entry_uidx;
+  uint8_t* covered;
+  uint32_t* out_u;
+  uint32_t* out_gain;
+  uint32_t* ctl;  // [3] rounds done
+};
+
+__global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams P) {
+  extern __shared__ unsigned long long gkey[];  // per: largest key of each owned group
+  __shared__ unsigned long long red[33];
+  __shared__ unsigned long long cta_best;
+  cg::cluster_group cluster = cg::this_cluster();
+  const uint32_t rank = cluster.block_rank();
+  const uint32_t C = cluster.num_blocks();
+  const uint32_t per = P.per_cta;
+  const uint32_t words = (per + 31) / 32;
+  uint32_t* dbits = reinterpret_cast<uint32_t*>(gkey + per);  // dirty bits of the owned groups
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t gbase = rank * per;
+  const uint32_t gend = min(P.NG, gbase + per);
+  const uint32_t nown = gend > gbase ? gend - gbase : 0;
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dbits[i] = 0xFFFFFFFFu;
+  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) gkey[i] = 0;
+  cluster.sync();
+  const uint32_t gsz = 1u << P.gshift;
+  int32_t r = 0;
+  for (; r < P.k; ++r) {
+    // 1. refresh the owned groups whose counts changed (one warp per word of dirty bits)
+    for (uint32_t wi = w; wi < words; wi += nw) {
+      uint32_t bits = dbits[wi];
+      __syncwarp();
+      if (!bits) continue;
+      if (lane == 0) dbits[wi] = 0;
+      while (bits) {
+        const uint32_t b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const uint32_t gl = wi * 32 + b;
+        if (gl >= nown) continue;
+        const uint32_t e0 = (gbase + gl) << P.gshift;
+        const uint32_t e1 = min(P.U, e0 + gsz);
+        unsigned long long best = 0;
+        for (uint32_t u = e0 + lane; u < e1; u += 32) {
+          const unsigned long long key = elem_key(__ldcg(&P.cnt[u]), u);
+          best = key > best ? key : best;
+        }
+        best = warp_max_u64(best);
+        if (lane == 0) gkey[gl] = best;
+      }
+    }
+    __syncthreads();
+    // 2. cluster-wide argmax of (count, smallest id)
+    unsigned long long key = 0;
+    for (uint32_t gl = threadIdx.x; gl < nown; gl += blockDim.x) key = gkey[gl] > key ? gkey[gl] : key;
+    key = block_max_u64(key, red);
+    if (threadIdx.x == 0) cta_best = key;
+    cluster.sync();
+    key = 0;
+    if (threadIdx.x < C) key = *cluster.map_shared_rank(&cta_best, threadIdx.x);
+    key = block_max_u64(key, red);
+    const uint32_t gain = (uint32_t)(key >> 32);
+    if (gain == 0) break;  // every remaining gain is zero: the same decision in every CTA
+    const uint32_t u = 0xFFFFFFFFu - (uint32_t)key;
+    if (rank == 0 && threadIdx.x == 0) {
+      P.out_u[r] = u;
+      P.out_gain[r] = gain;
+      atomicOr(&P.cnt[u], EXCLUDED);
+    }
+    if (threadIdx.x == 0) {  // the picked element's group is dirty in its owner
+      const uint32_t gg = u >> P.gshift;
+      if (gg / per == rank) atomicOr(&dbits[(gg % per) >> 5], 1u << ((gg % per) & 31));
+    }
+    // 3. cover its walks (one warp per walk): decrement every element of each newly
+    //    covered walk and mark the element's group dirty in the CTA that owns it
+    const uint32_t q0 = P.inv_off[u], q1 = P.inv_off[u + 1];
+    for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
+      const uint32_t j = P.inv_walk[q];
+      uint32_t fresh = 0;
+      if (lane == 0) {
+        fresh = __ldcg(&P.covered[j]) ? 0u : 1u;
+        if (fresh) P.covered[j] = 1;
+      }
+      fresh = __shfl_sync(0xffffffffu, fresh, 0);
+      if (!fresh) continue;
+      const uint32_t p1 = P.walk_eoff[j + 1];
+      for (uint32_t p = P.walk_eoff[j] + lane; p < p1; p += 32) {
+        const uint32_t x = P.entry_uidx[p];
+        atomicSub(&P.cnt[x], 1u);
+        const uint32_t gg = x >> P.gshift, gl = gg % per;
+        uint32_t* rb = cluster.map_shared_rank(dbits, gg / per);
+        atomicOr(&rb[gl >> 5], 1u << (gl & 31));
+      }
+    }
+    cluster.sync();
+  }
+  cluster.sync();  // no CTA leaves while a peer may still read its shared memory
+  if (rank == 0 && threadIdx.x == 0) P.ctl[3] = (uint32_t)r;
+}
+
+__global__ void k_greedy_init(const int32_t* __restrict__ uid, const uint32_t* __restrict__ cnt, uint32_t U,
+                              const uint8_t* __restrict__ cand, uint32_t* __restrict__ cnt_work) {
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
-    allowed[u] = cand ? (cand[uid[u]] ? 1 : 0) : 1;
+    cnt_work[u] = cnt[u] | ((cand && !cand[uid[u]]) ? EXCLUDED : 0u);
 }
 
 __global__ void k_pick_ids(const uint32_t* __restrict__ out_u, const int32_t* __restrict__ uid, int32_t r,
@@ -315,6 +469,106 @@ static int greedy_grid() {
   return cached;
 }
 
+// Launch the cluster greedy when one cluster's shared memory holds the group maxima;
+// *done = false leaves the grid-wide version to run.
+static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k, uint32_t* outs, uint32_t* ctl,
+                                  int32_t* rounds, bool* done, cudaStream_t s) {
+  *done = false;
+  const char* force = getenv("HSAW_GREEDY");  // "grid" selects the grid-wide version (tests)
+  if (force && force[0] == 'g') return HSAW_OK;
+  static int cluster_size = -1;
+  static size_t smem_cap = 0;
+  if (cluster_size < 0) {
+    cluster_size = 0;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    smem_cap = optin > 16384 ? (size_t)optin - 12288 : 0;  // keep room for the static shared arrays
+    if (cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) == cudaSuccess) {
+      const int want[2] = {16, 8};
+      for (int i = 0; i < 2 && !cluster_size; ++i) {
+        if (want[i] > 8 &&
+            cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = want[i];
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(want[i]);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smem_cap;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_greedy_cluster, &cfg) == cudaSuccess && nclusters > 0)
+          cluster_size = want[i];
+        else
+          cudaGetLastError();
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (!cluster_size) return HSAW_OK;
+  const uint32_t U = (uint32_t)cv.unique;
+  // smallest group size whose keys fit: per_cta * 8 + per_cta / 8 bytes per CTA
+  uint32_t gshift = 8;
+  uint32_t NG = 0, per = 0;
+  for (;; ++gshift) {
+    NG = (uint32_t)(((uint64_t)U + (1ull << gshift) - 1) >> gshift);
+    per = (NG + cluster_size - 1) / cluster_size;
+    const size_t need = (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64;
+    if (need <= smem_cap) break;
+    if (gshift >= 20) return HSAW_OK;
+  }
+  const size_t smem = (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64;
+  HSAW_TRY(cv.cnt_work.ensure(U, s));
+  HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
+  HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
+  count_launch();
+  k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);
+  HSAW_CK(cudaGetLastError());
+  ClusterGreedyParams P;
+  P.U = U;
+  P.NG = NG;
+  P.per_cta = per;
+  P.gshift = gshift;
+  P.k = k;
+  P.cnt = cv.cnt_work.p;
+  P.inv_off = cv.inv_off.p;
+  P.inv_walk = cv.inv_walk.p;
+  P.walk_eoff = cv.walk_eoff.p;
+  P.entry_uidx = cv.entry_uidx.p;
+  P.covered = cv.covered.p;
+  P.out_u = outs;
+  P.out_gain = outs + k;
+  P.ctl = ctl;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster_size;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cluster_size);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  count_launch();
+  HSAW_CK(cudaLaunchKernelEx(&cfg, k_greedy_cluster, P));
+  uint32_t h[4];
+  HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  *rounds = (int32_t)h[3];
+  *done = true;
+  return HSAW_OK;
+}
+
 hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t k, int64_t* ids_host,
                          uint32_t* gains_host, cudaStream_t s) {
   if (k < 1) return fail(HSAW_E_INVALID, "greedy: k < 1");
@@ -327,19 +581,30 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
   HSAW_CK(cudaMemsetAsync(ctl, 0, 8 * sizeof(uint32_t), s));
   int32_t rounds = 0;
   hsaw_status st = HSAW_OK;
+  bool done = false;
   if (U > 0 && cv.walks > 0) {
+    st = cluster_greedy(cv, cand_dev, k, outs.p, ctl, &rounds, &done, s);
+    if (st == HSAW_OK && done && rounds > 0) {
+      count_launch();
+      k_pick_ids<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(outs.p, cv.uid.p, rounds, ids.p);
+      if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: id launch failed");
+    }
+  }
+  if (st == HSAW_OK && !done && U > 0 && cv.walks > 0) {
     const int G = greedy_grid();
+    const uint32_t NG = (U + GREEDY_GROUP - 1) / GREEDY_GROUP;
     HSAW_TRY(cv.cnt_work.ensure(U, s));
-    HSAW_TRY(cv.allowed.ensure(U, s));
+    HSAW_TRY(cv.dirty.ensure(NG, s));
     HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
-    HSAW_TRY(cv.partial.ensure(G, s));
-    HSAW_CK(cudaMemcpyAsync(cv.cnt_work.p, cv.cnt.p, (size_t)U * 4, cudaMemcpyDeviceToDevice, s));
+    HSAW_TRY(cv.partial.ensure((size_t)G + NG, s));
     HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
+    HSAW_CK(cudaMemsetAsync(cv.dirty.p, 1, NG, s));
     count_launch();
-    k_allowed<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, U, cand_dev, cv.allowed.p);
+    k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);
     HSAW_CK(cudaGetLastError());
     GreedyParams P;
     P.U = U;
+    P.NG = NG;
     P.k = k;
     P.cnt = cv.cnt_work.p;
     P.inv_off = cv.inv_off.p;
@@ -347,8 +612,9 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
     P.walk_eoff = cv.walk_eoff.p;
     P.entry_uidx = cv.entry_uidx.p;
     P.covered = cv.covered.p;
-    P.allowed = cv.allowed.p;
+    P.dirty = cv.dirty.p;
     P.partial = cv.partial.p;
+    P.gkey = cv.partial.p + G;
     P.out_u = outs.p;
     P.out_gain = outs.p + k;
     P.ctl = ctl;

@@ -17,6 +17,11 @@ struct Timed {
   uint64_t attempts;
 };
 static std::vector<Timed> g_timed;
+struct PhaseTimed {
+  cudaEvent_t a, b;
+  int phase;
+};
+static std::vector<PhaseTimed> g_phase;
 static uint64_t g_steps = 0, g_sampler_launches = 0, g_attempts = 0;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -45,6 +50,28 @@ void profile_end(void* token, cudaStream_t s, uint64_t attempts) {
   delete t;
 }
 
+void* phase_begin(cudaStream_t s) {
+  if (!g_enabled.load()) return nullptr;
+  PhaseTimed* t = new PhaseTimed();
+  if (cudaEventCreate(&t->a) != cudaSuccess || cudaEventCreate(&t->b) != cudaSuccess) {
+    cudaGetLastError();
+    delete t;
+    return nullptr;
+  }
+  cudaEventRecord(t->a, s);
+  return t;
+}
+
+void phase_end(void* token, cudaStream_t s, int phase) {
+  if (!token) return;
+  PhaseTimed* t = static_cast<PhaseTimed*>(token);
+  cudaEventRecord(t->b, s);
+  t->phase = phase;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_phase.push_back(*t);
+  delete t;
+}
+
 void profile_add_steps(uint64_t steps) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_steps += steps;
@@ -63,6 +90,11 @@ hsaw_status hsaw_profile_enable(int on) {
     cudaEventDestroy(t.b);
   }
   g_timed.clear();
+  for (auto& t : g_phase) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  g_phase.clear();
   g_steps = g_sampler_launches = g_attempts = 0;
   g_launches.store(0);
   g_enabled.store(on ? 1 : 0);
@@ -77,6 +109,12 @@ hsaw_status hsaw_profile_read(hsaw_profile* out) {
   for (auto& t : g_timed) {
     float x = 0.f;
     if (cudaEventElapsedTime(&x, t.a, t.b) == cudaSuccess) ms += x;
+    else cudaGetLastError();
+  }
+  for (int i = 0; i < 8; ++i) out->phase_ms[i] = 0.0;
+  for (auto& t : g_phase) {
+    float x = 0.f;
+    if (t.phase >= 0 && t.phase < 8 && cudaEventElapsedTime(&x, t.a, t.b) == cudaSuccess) out->phase_ms[t.phase] += x;
     else cudaGetLastError();
   }
   out->kernel_launches = g_launches.load();

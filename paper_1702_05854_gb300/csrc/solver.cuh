@@ -59,7 +59,7 @@ struct Cover {
   DBuf<uint32_t> entry_uidx;                // entries: unique index of each walk entry
   DBuf<uint32_t> walk_eoff;                 // walks + 1: entry offsets of the walks
   DBuf<uint32_t> cnt_work;                  // greedy's running counts
-  DBuf<uint8_t> covered, allowed;
+  DBuf<uint8_t> covered, dirty;  // greedy: walk covered flags, group dirty flags
   DBuf<unsigned long long> partial;
   DBuf<uint32_t> misc;
   void release(cudaStream_t s);

@@ -214,6 +214,16 @@ def test_greedy_matches_oracle(c1_stream, mode, k):
     assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
 
 
+def test_greedy_grid_version_matches_oracle(c1_stream, monkeypatch):
+    """The grid-wide greedy (used when a cluster cannot hold the group maxima) agrees too."""
+    monkeypatch.setenv("HSAW_GREEDY", "grid")
+    d, g, og, w, st = c1_stream
+    for mode, M, k in ((hs.HSAW_EDGE, d["m"], 40), (hs.HSAW_NODE, d["n"], 25)):
+        ids, gains = hs.hsaw_greedy(w, g, mode, 100, 15_000, k)
+        oids, ogains = st.greedy(mode, 100, 15_000, M, k)
+        assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
+
+
 def test_greedy_zero_gain_fill():
     # every walk is covered after one pick; the rest are zero-gain smallest-id candidates
     n = 5
