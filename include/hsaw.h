@@ -133,6 +133,42 @@ typedef struct {
  * HSAW_E_NOMEM, HSAW_E_DEVICE, HSAW_E_STEP_CAP, HSAW_E_TIMEOUT. */
 HSAW_API hsaw_status hsaw_solve(hsaw_graph g, const hsaw_query* q, hsaw_result* r, void* stream);
 
+/* ------------------------------------------------------------------ batched and served solves
+ * Not in the paper: many interdiction instances at once (batching) and a request loop
+ * (serving).  Every instance runs exactly the hsaw_solve computation on its own CUDA
+ * stream, so each result is bit-identical to the instance solved alone.
+ *
+ * hsaw_solve_batch: solve count instances (gs[i], qs[i]) -> rs[i] (caller buffers as in
+ *   hsaw_solve), statuses[i] (may be NULL) the status of each.  `concurrency` worker
+ *   threads (<= 0: 8), each with its own non-blocking stream, take the instances in index
+ *   order; `stream` is synchronised first.  Returns HSAW_OK when every instance
+ *   succeeded, else the first failing status (the other results stay valid).
+ *
+ * Server (continuous batching): hsaw_server_create keeps the graphs (not owned: they
+ *   must outlive the server) and starts `workers` threads (<= 0: 8).  mem_budget (bytes,
+ *   0 = 3/4 of the free device memory at creation) bounds the summed device-memory
+ *   estimates of the queries on the GPU.  hsaw_server_submit copies the query's host
+ *   arrays and returns a ticket; a query whose estimate alone exceeds the budget is
+ *   refused with HSAW_E_REJECTED.  Queries start in submission order as soon as a worker
+ *   is free and the budget has room, while earlier ones are still running.
+ *   hsaw_server_poll waits up to timeout_ms (< 0: forever) for the ticket: HSAW_E_TIMEOUT
+ *   if still running (the ticket stays valid), else the query's own status, with r
+ *   filled as by hsaw_solve and *latency_ms (may be NULL) = completion - submission;
+ *   the ticket is then released.  hsaw_server_cancel: a queued query never starts, a
+ *   running one stops at its next sampler launch or stopping-rule round; its poll
+ *   returns HSAW_E_CANCELLED.  hsaw_server_destroy cancels what is left, joins the
+ *   workers and frees the server. */
+typedef struct hsaw_server_s* hsaw_server;
+HSAW_API hsaw_status hsaw_solve_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_result* rs,
+                                      hsaw_status* statuses, int32_t count, int32_t concurrency, void* stream);
+HSAW_API hsaw_status hsaw_server_create(const hsaw_graph* gs, int32_t n_graphs, size_t mem_budget, int32_t workers,
+                                        hsaw_server* out);
+HSAW_API hsaw_status hsaw_server_submit(hsaw_server s, int32_t graph_idx, const hsaw_query* q, uint64_t* ticket);
+HSAW_API hsaw_status hsaw_server_poll(hsaw_server s, uint64_t ticket, hsaw_result* r, int32_t timeout_ms,
+                                      double* latency_ms);
+HSAW_API hsaw_status hsaw_server_cancel(hsaw_server s, uint64_t ticket);
+HSAW_API hsaw_status hsaw_server_destroy(hsaw_server s);
+
 /* ------------------------------------------------------------------ the stream R (Alg. 3)
  * hsaw_sample: draw the first n_hits HSAWs of the query's stream, attempts
  *   first_attempt, first_attempt + 1, ... (only sources, p_fixed, seed and max_attempts

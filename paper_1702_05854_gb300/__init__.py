@@ -71,6 +71,12 @@ SIGNATURES = {
     "hsaw_stop_constants": (ctypes.c_int, [_i64, _i32, _dbl, _dbl, _p]),
     "hsaw_check": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, _dbl, _dbl, ctypes.POINTER(_dbl)]),
     "hsaw_sample_hits_static": (ctypes.c_int, [_p, _p, _u64, _u64, _i64, _p, _p, _i64, ctypes.POINTER(_i64), _p]),
+    "hsaw_solve_batch": (ctypes.c_int, [_p, _p, _p, _p, _i32, _i32, _p]),
+    "hsaw_server_create": (ctypes.c_int, [_p, _i32, ctypes.c_size_t, _i32, ctypes.POINTER(_p)]),
+    "hsaw_server_submit": (ctypes.c_int, [_p, _i32, ctypes.POINTER(hsaw_query), ctypes.POINTER(_u64)]),
+    "hsaw_server_poll": (ctypes.c_int, [_p, _u64, ctypes.POINTER(hsaw_result), _i32, ctypes.POINTER(_dbl)]),
+    "hsaw_server_cancel": (ctypes.c_int, [_p, _u64]),
+    "hsaw_server_destroy": (ctypes.c_int, [_p]),
     "hsaw_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "hsaw_profile_read": (ctypes.c_int, [ctypes.POINTER(hsaw_profile)]),
     "hsaw_last_error": (ctypes.c_char_p, []),
@@ -240,8 +246,76 @@ def hsaw_solve(graph: Graph, query: Query, stream=None):
     r.gains = _ptr(gains)
     q = query.c()
     _check(load().hsaw_solve(graph.handle, ctypes.byref(q), ctypes.byref(r), _stream(stream)))
-    d = {f: getattr(r, f) for f, _ in hsaw_result._fields_ if f not in ("ids", "gains")}
-    return ids, gains, d
+    return ids, gains, _result_dict(r)
+
+
+def _result_dict(r):
+    return {f: getattr(r, f) for f, _ in hsaw_result._fields_ if f not in ("ids", "gains")}
+
+
+def hsaw_solve_batch(graphs, queries, concurrency: int = 0, stream=None):
+    """Solve instances (graphs[i], queries[i]) concurrently; returns a list of
+    (status, ids, gains, result dict) in instance order."""
+    n = len(queries)
+    qa = (hsaw_query * n)(*[q.c() for q in queries])
+    ra = (hsaw_result * n)()
+    outs = []
+    for i, q in enumerate(queries):
+        ids = np.empty(q.k, np.int64)
+        gains = np.empty(q.k, np.uint32)
+        ra[i].ids = _ptr(ids)
+        ra[i].gains = _ptr(gains)
+        outs.append((ids, gains))
+    ga = (ctypes.c_void_p * n)(*[g.handle for g in graphs])
+    st = (ctypes.c_int * n)()
+    load().hsaw_solve_batch(ga, qa, ra, st, n, concurrency, _stream(stream))
+    return [(int(st[i]), outs[i][0], outs[i][1], _result_dict(ra[i])) for i in range(n)]
+
+
+class Server:
+    """Continuous-batching server over resident graphs (hsaw_server handle)."""
+
+    def __init__(self, graphs, mem_budget: int = 0, workers: int = 0):
+        self._graphs = list(graphs)
+        ga = (ctypes.c_void_p * len(graphs))(*[g.handle for g in graphs])
+        h = ctypes.c_void_p()
+        _check(load().hsaw_server_create(ga, len(graphs), mem_budget, workers, ctypes.byref(h)))
+        self._h = h
+        self._k = {}
+
+    def submit(self, graph_idx: int, query: Query) -> int:
+        q = query.c()
+        t = _u64()
+        _check(load().hsaw_server_submit(self._h, graph_idx, ctypes.byref(q), ctypes.byref(t)))
+        self._k[t.value] = query.k
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """(ids, gains, result dict, latency_ms); raises HsawError (HSAW_E_TIMEOUT while running)."""
+        k = self._k[ticket]
+        ids = np.empty(k, np.int64)
+        gains = np.empty(k, np.uint32)
+        r = hsaw_result()
+        r.ids = _ptr(ids)
+        r.gains = _ptr(gains)
+        lat = _dbl()
+        rc = load().hsaw_server_poll(self._h, ticket, ctypes.byref(r), timeout_ms, ctypes.byref(lat))
+        if rc != -7:
+            self._k.pop(ticket, None)
+        _check(rc)
+        return ids, gains, _result_dict(r), lat.value
+
+    def cancel(self, ticket: int):
+        _check(load().hsaw_server_cancel(self._h, ticket))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.hsaw_server_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class Walks:

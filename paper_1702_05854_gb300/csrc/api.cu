@@ -89,6 +89,10 @@ static hsaw_status aid_at(const Stream& st, int64_t j, uint64_t* out, cudaStream
   return HSAW_OK;
 }
 
+static thread_local const volatile int* t_cancel = nullptr;
+void set_cancel_flag(const volatile int* flag) { t_cancel = flag; }
+bool cancel_requested() { return t_cancel && *t_cancel; }
+
 static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cudaStream_t s) {
   if (!q || !r || !r->ids || !r->gains) return fail(HSAW_E_INVALID, "solve: NULL argument");
   int64_t n_cand = 0;
@@ -134,6 +138,7 @@ static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cu
     std::vector<int64_t> ids(k);
     std::vector<uint32_t> gains(k);
     for (int32_t t = 1;; ++t) {
+      if (cancel_requested()) return fail(HSAW_E_CANCELLED, "solve: query cancelled");
       if (t > 40 || (L << (t - 1)) > (int64_t)1 << 30) return fail(HSAW_E_NOMEM, "stop rule: sample budget beyond device limits");
       const int64_t half = L << (t - 1);
       void* ph = phase_begin(s);
@@ -178,6 +183,10 @@ static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cu
   }
   r->steps = W.st.steps;
   return HSAW_OK;
+}
+
+hsaw_status solve_one(const Graph& g, const hsaw_query* q, hsaw_result* r, cudaStream_t s) {
+  return solve(g, q, r, s);
 }
 
 }  // namespace hsaw

@@ -460,12 +460,11 @@ __global__ void __launch_bounds__(1024) k_zero_fill(int64_t M, const uint8_t* __
 }
 
 static int greedy_grid() {
-  static int cached = 0;
-  if (!cached) {
+  static const int cached = [] {
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_greedy, 512, 0);
-    cached = std::max(1, std::min(b, 2)) * sm_count();
-  }
+    return std::max(1, std::min(b, 2)) * sm_count();
+  }();
   return cached;
 }
 
@@ -476,43 +475,49 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   *done = false;
   const char* force = getenv("HSAW_GREEDY");  // "grid" selects the grid-wide version (tests)
   if (force && force[0] == 'g') return HSAW_OK;
-  static int cluster_size = -1;
-  static size_t smem_cap = 0;
-  if (cluster_size < 0) {
-    cluster_size = 0;
+  struct ClusterCfg {
+    int size = 0;
+    size_t smem_cap = 0;
+  };
+  static const ClusterCfg cfg0 = [] {
+    ClusterCfg c;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    smem_cap = optin > 16384 ? (size_t)optin - 12288 : 0;  // keep room for the static shared arrays
-    if (cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) == cudaSuccess) {
-      const int want[2] = {16, 8};
-      for (int i = 0; i < 2 && !cluster_size; ++i) {
-        if (want[i] > 8 &&
-            cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-          cudaGetLastError();
-          continue;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = want[i];
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(want[i]);
-        cfg.blockDim = dim3(1024);
-        cfg.dynamicSmemBytes = smem_cap;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_greedy_cluster, &cfg) == cudaSuccess && nclusters > 0)
-          cluster_size = want[i];
-        else
-          cudaGetLastError();
-      }
-    } else {
+    c.smem_cap = optin > 16384 ? (size_t)optin - 12288 : 0;  // keep room for the static shared arrays
+    if (cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_cap) !=
+        cudaSuccess) {
       cudaGetLastError();
+      return c;
     }
-  }
+    const int want[2] = {16, 8};
+    for (int i = 0; i < 2 && !c.size; ++i) {
+      if (want[i] > 8 &&
+          cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = want[i];
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(want[i]);
+      cfg.blockDim = dim3(1024);
+      cfg.dynamicSmemBytes = c.smem_cap;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_greedy_cluster, &cfg) == cudaSuccess && nclusters > 0)
+        c.size = want[i];
+      else
+        cudaGetLastError();
+    }
+    return c;
+  }();
+  const int cluster_size = cfg0.size;
+  const size_t smem_cap = cfg0.smem_cap;
   if (!cluster_size) return HSAW_OK;
   const uint32_t U = (uint32_t)cv.unique;
   // smallest group size whose keys fit: per_cta * 8 + per_cta / 8 bytes per CTA

@@ -10,13 +10,12 @@
 namespace hsaw {
 
 int sm_count() {
-  static int cached = 0;
-  if (!cached) {
+  static const int cached = [] {  // thread-safe one-time initialisation
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cached = v > 0 ? v : 1;
-  }
+    return v > 0 ? v : 1;
+  }();
   return cached;
 }
 

@@ -346,12 +346,11 @@ static SampleParams make_params(const Graph& g, const QueryDev& qd) {
 }
 
 static int sample_blocks_per_sm() {
-  static int cached = 0;
-  if (!cached) {
+  static const int cached = [] {
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample<false, false>, 256, 0);
-    cached = b > 0 ? b : 1;
-  }
+    return b > 0 ? b : 1;
+  }();
   return cached;
 }
 
@@ -369,6 +368,7 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
   unsigned long long* d_steps = nullptr;
   HSAW_TRY(st.tmp64.ensure(1, s));
   while (st.count < want) {
+    if (cancel_requested()) return fail(HSAW_E_CANCELLED, "sampling: query cancelled");
     const uint64_t used = st.next_attempt - st.first_attempt;
     if (used >= st.max_attempts) return fail(HSAW_E_TIMEOUT, "sampling: attempt budget exhausted before enough hits");
     // launch size from the hit rate so far (2^20 .. 2^28 attempts; doubling while no hit)

@@ -73,6 +73,14 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
 hsaw_status cover_count(const Stream& st, hsaw_mode mode, int64_t first, int64_t count, const int64_t* T, int32_t k,
                         uint64_t* cov, cudaStream_t s);
 
+// Cancellation of the calling thread's current solve (set by the server's workers):
+// checked between sampler launches and between stopping-rule rounds.
+void set_cancel_flag(const volatile int* flag);
+bool cancel_requested();
+
+// One full solve on `s` (the body of hsaw_solve).
+hsaw_status solve_one(const Graph& g, const hsaw_query* q, hsaw_result* r, cudaStream_t s);
+
 // Stopping-rule constants (Sec. 5.1) and Check (Alg. 5), host FP64.
 void stop_constants(int64_t M, int32_t k, double eps, double delta, double out6[6]);
 int check_bound(double c, double cp, double size_rp, int32_t t, double eps, double lambda1, double* eps_t);
