@@ -156,6 +156,159 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def same_result(a, b):
+    """Equal result counters and estimates (NaN equal to NaN)."""
+    for key in a:
+        x, y = a[key], b[key]
+        if isinstance(x, float) and x != x:
+            if y == y:
+                return False
+        elif x != y:
+            return False
+    return True
+
+
+def batch_workload(count, n_max, n_hsaw, seed=1):
+    """256 Chung-Lu instances: n log-uniform [1e3, n_max], average degree uniform [8, 32],
+    |S| log-uniform [1, 1000], k uniform [10, 500] (clipped to |C|), eSI/nSI alternating,
+    N HSAWs each (the batched configuration)."""
+    rng = np.random.default_rng(seed)
+    inst = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(n_max))))
+        deg = int(rng.integers(8, 33))
+        src, dst = synth.chung_lu_graph(n, n * deg, 2.1, seed=1000 + i)
+        w = synth.wc_weights(n, dst)
+        ns = int(min(n, max(1, round(np.exp(rng.uniform(0, np.log(1000)))))))
+        mode = "edge" if i % 2 == 0 else "node"
+        M = n * deg if mode == "edge" else n
+        k = int(min(M, rng.integers(10, 501)))
+        inst.append(dict(n=n, m=n * deg, src=src, dst=dst, w=w, sources=synth.sources(n, ns, seed=2000 + i),
+                         mode=mode, k=k, n_hsaw=n_hsaw, seed=synth.SEED_WALKS + i))
+    return inst
+
+
+def run_batch_mode(args, hs, torch):
+    t0 = time.time()
+    inst = batch_workload(args.batch_count, args.batch_nmax, args.batch_nhsaw)
+    gen_s = time.time() - t0
+    graphs = [hs.hsaw_graph_from_edges(x["n"], x["src"], x["dst"], x["w"]) for x in inst]
+    queries = [hs.Query(sources=x["sources"], mode=hs.HSAW_EDGE if x["mode"] == "edge" else hs.HSAW_NODE, k=x["k"],
+                        n_hsaw=x["n_hsaw"], seed=x["seed"]) for x in inst]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # warm-up: a few instances each way
+    for g, q in list(zip(graphs, queries))[:3]:
+        hs.hsaw_solve(g, q)
+    hs.hsaw_solve_batch(graphs[:8], queries[:8], concurrency=args.batch_workers)
+    clocks = Clocks(0)
+    clocks.start()
+    e0.record(stream)
+    serial = [hs.hsaw_solve(g, q) for g, q in zip(graphs, queries)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_serial = e0.elapsed_time(e1) / 1e3
+    hs.hsaw_profile_enable(True)
+    e0.record(stream)
+    batched = hs.hsaw_solve_batch(graphs, queries, concurrency=args.batch_workers)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    prof = hs.hsaw_profile_read()
+    hs.hsaw_profile_enable(False)
+    ck = clocks.stop()
+    identical = all(st == 0 and np.array_equal(ids, a[0]) and np.array_equal(gains, a[1]) and same_result(r, a[2])
+                    for (st, ids, gains, r), a in zip(batched, serial))
+    n = len(inst)
+    line = {"metric": f"batched SI solves/s ({n} Chung-Lu eSI/nSI instances, N={args.batch_nhsaw} HSAWs each)",
+            "value": n / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batched", "instances": n, "n_range": [1000, args.batch_nmax],
+                       "avg_degree": [8, 32], "sources": [1, 1000], "k": [10, 500], "n_hsaw": args.batch_nhsaw,
+                       "workers": args.batch_workers, "graph_gen_s": gen_s,
+                       "edges_total": int(sum(x["m"] for x in inst))},
+            "serial_solves_per_s": n / t_serial, "batched_vs_serial": t_serial / t_batch,
+            "identical_to_serial": bool(identical), "gpu_launches": prof["kernel_launches"],
+            "device_ms_by_phase_batched": prof["phase_ms"], "clocks": ck}
+    print(json.dumps(line), flush=True)
+
+
+def serve_queries(count, graphs_meta, min_sources, seed=5):
+    """Serving queries: graph uniform, |S| log-uniform [lo, 1000], k log-uniform [10, 1000],
+    eSI or nSI uniform, eps in {0.1, 0.2}, stopping rule."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        gi = int(rng.integers(0, len(graphs_meta)))
+        n, m = graphs_meta[gi]
+        ns = int(round(np.exp(rng.uniform(np.log(min_sources), np.log(1000)))))
+        mode = int(rng.integers(0, 2))
+        k = int(round(np.exp(rng.uniform(np.log(10), np.log(1000)))))
+        eps = float(rng.choice([0.1, 0.2]))
+        out.append((gi, dict(sources=synth.sources(n, ns, seed=7000 + i), mode=mode, k=min(k, n if mode else m),
+                             sampling=1, eps=eps, seed=synth.SEED_WALKS + i)))
+    return out
+
+
+def run_serve_mode(args, hs, torch):
+    scales = [int(x) for x in args.serve_scales.split(",")]
+    gm, graphs = [], []
+    for sc in scales:
+        src, dst = synth.rmat_graph(sc, 16, seed=synth.SEED_GRAPH)
+        n = 1 << sc
+        graphs.append(hs.hsaw_graph_from_edges(n, src, dst, synth.wc_weights(n, dst)))
+        gm.append((n, int(src.shape[0])))
+    qs = serve_queries(args.serve_queries, gm, args.serve_min_sources)
+    queries = [(gi, hs.Query(**kw)) for gi, kw in qs]
+    # serial: one query at a time on the same stream of queries
+    hs.hsaw_solve(graphs[queries[0][0]], queries[0][1])
+    t0 = time.perf_counter()
+    alone = [hs.hsaw_solve(graphs[gi], q) for gi, q in queries]
+    t_serial = time.perf_counter() - t0
+    serial_rate = len(queries) / t_serial
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    per_rate = []
+    identical = True
+    clocks = Clocks(0)
+    clocks.start()
+    for rate in rates:
+        srv = hs.Server(graphs, workers=args.serve_workers)
+        rng = np.random.default_rng(int(rate))
+        gaps = rng.exponential(1.0 / rate, size=len(queries))
+        tickets = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for (gi, q), gap in zip(queries, gaps):
+            t_next += gap
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(gi, q))
+        lats = []
+        for t, a in zip(tickets, alone):
+            ids, gains, r, lat = srv.poll(t)
+            lats.append(lat)
+            identical &= bool(np.array_equal(ids, a[0]) and np.array_equal(gains, a[1]) and same_result(r, a[2]))
+        t_end = time.perf_counter()
+        srv.close()
+        per_rate.append({"offered_qps": rate, "solves_per_s": len(queries) / (t_end - t_start),
+                         "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99))})
+    ck = clocks.stop()
+    best = max(per_rate, key=lambda x: x["solves_per_s"])
+    line = {"metric": "served SI solves/s and p50/p99 latency (Poisson arrivals)", "value": best["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": len(rates), "warmup": 1,
+            "ms_per_step": 1e3 / best["solves_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "serving", "graphs": [f"rmat{sc}-wc" for sc in scales],
+                       "queries_per_rate": len(queries), "sources": [args.serve_min_sources, 1000], "k": [10, 1000],
+                       "eps": [0.1, 0.2], "workers": args.serve_workers},
+            "serial_solves_per_s": serial_rate, "served_vs_serial": best["solves_per_s"] / serial_rate,
+            "per_rate": per_rate, "identical_to_alone": bool(identical), "clocks": ck}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +320,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-attempts", type=int, default=50_000)
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-nmax", type=float, default=1e6)
+    ap.add_argument("--batch-nhsaw", type=int, default=100_000)
+    ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--serve-scales", default="18,20")
+    ap.add_argument("--serve-queries", type=int, default=200)
+    ap.add_argument("--serve-rates", default="10,30,100,300")
+    ap.add_argument("--serve-workers", type=int, default=16)
+    ap.add_argument("--serve-min-sources", type=int, default=16)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -179,6 +342,10 @@ def main():
     import paper_1702_05854_gb300 as hs
 
     torch.cuda.set_device(local)
+    if args.mode == "batch":
+        return run_batch_mode(args, hs, torch)
+    if args.mode == "serve":
+        return run_serve_mode(args, hs, torch)
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -520,17 +520,21 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   const size_t smem_cap = cfg0.smem_cap;
   if (!cluster_size) return HSAW_OK;
   const uint32_t U = (uint32_t)cv.unique;
-  // smallest group size whose keys fit: per_cta * 8 + per_cta / 8 bytes per CTA
-  uint32_t gshift = 8;
-  uint32_t NG = 0, per = 0;
-  for (;; ++gshift) {
-    NG = (uint32_t)(((uint64_t)U + (1ull << gshift) - 1) >> gshift);
-    per = (NG + cluster_size - 1) / cluster_size;
-    const size_t need = (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64;
-    if (need <= smem_cap) break;
-    if (gshift >= 20) return HSAW_OK;
+  // the smallest cluster (fewest SMs, cheapest barrier) whose shared memory holds the keys
+  // of 256-element groups; beyond the largest cluster, larger groups
+  auto need = [](uint32_t per) { return (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64; };
+  uint32_t gshift = 8, csize = 1;
+  uint32_t NG = (uint32_t)(((uint64_t)U + 255) >> 8), per = NG;
+  while (need(per) > smem_cap && (int)csize < cluster_size) {
+    csize *= 2;
+    per = (NG + csize - 1) / csize;
   }
-  const size_t smem = (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64;
+  while (need(per) > smem_cap) {
+    if (++gshift > 20) return HSAW_OK;
+    NG = (uint32_t)(((uint64_t)U + (1ull << gshift) - 1) >> gshift);
+    per = (NG + csize - 1) / csize;
+  }
+  const size_t smem = need(per);
   HSAW_TRY(cv.cnt_work.ensure(U, s));
   HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
   HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
@@ -555,10 +559,10 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cluster_size;
+  at[0].val.clusterDim.x = csize;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(cluster_size);
+  cfg.gridDim = dim3(csize);
   cfg.blockDim = dim3(1024);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
