@@ -33,6 +33,7 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "HSAWs/s at 1B edges (eSI stop-rule solve, R-MAT scale 26)"
+METRIC_OTHER = {"c2": "HSAWs/s (nSI R-MAT 20 random LT, N = 10 M)", "c1": "HSAWs/s (eSI Chung-Lu 16 K, N = 200 K)"}
 UNIT = "HSAW/s"
 BYTES_PER_STEP = 96  # three random 32-byte sectors per live-edge draw: node record, threshold, tail node
 # DRAM bytes per attempt of the sampler kernel from an ncu capture, keyed by the hash of
@@ -95,16 +96,25 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def make_workload(scale):
+def make_workload(scale, which="c3"):
+    """c3: the billion-edge eSI stop-rule solve (default); c2: the nSI R-MAT 20 random-LT
+    solve with N = 10 M HSAWs; c1: the eSI Chung-Lu 16 K solve with N = 200 K."""
     t0 = time.time()
-    d = synth.workload_c3(scale)
+    if which == "c2":
+        d = synth.workload_c2()
+    elif which == "c1":
+        d = synth.workload_c1()
+    else:
+        d = synth.workload_c3(scale)
     d["gen_s"] = time.time() - t0
     return d
 
 
 def query_for(hs, d, seed):
-    return hs.Query(sources=d["sources"], mode=hs.HSAW_EDGE, k=d["k"], sampling=hs.HSAW_STOP_RULE, eps=d["eps"],
-                    seed=seed)
+    mode = hs.HSAW_EDGE if d["mode"] == "edge" else hs.HSAW_NODE
+    if "n_hsaw" in d:
+        return hs.Query(sources=d["sources"], mode=mode, k=d["k"], n_hsaw=d["n_hsaw"], seed=seed)
+    return hs.Query(sources=d["sources"], mode=mode, k=d["k"], sampling=hs.HSAW_STOP_RULE, eps=d["eps"], seed=seed)
 
 
 def cpu_baseline(d, seed, seconds):
@@ -133,7 +143,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    d = make_workload(args.scale)
+    d = make_workload(args.scale, args.workload)
     og = oracle.Graph(d["n"], d["src"], d["dst"], d["w"])
     q = oracle.Query(og, d["sources"], seed=synth.SEED_WALKS)
     per_step = args.ref_attempts
@@ -149,7 +159,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"]},
+            "config": {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"],
+                       "eps": d.get("eps"), "n_hsaw": d.get("n_hsaw"), "delta": "1/n", "parallelism": f"replicas{world}"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} attempts per step of the query stream"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -321,6 +332,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-attempts", type=int, default=50_000)
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-nmax", type=float, default=1e6)
     ap.add_argument("--batch-nhsaw", type=int, default=100_000)
@@ -351,7 +363,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    d = make_workload(args.scale)
+    d = make_workload(args.scale, args.workload)
     seed = synth.SEED_WALKS + rank
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -438,13 +450,16 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(d, seed, args.cpu_seconds)
+    gbytes = 16.0 * d["n"] + 56.0 * d["m"]  # node records + edge, walk-record and index arrays
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC_OTHER.get(args.workload, METRIC), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"],
-                   "eps": d["eps"], "delta": "1/n", "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (9.6 GB graph)", "hits_per_step": hits / args.steps,
+                   "eps": d.get("eps"), "n_hsaw": d.get("n_hsaw"), "delta": "1/n", "parallelism": f"replicas{world}",
+                   "l2": (f"inputs larger than L2 ({gbytes / 1e9:.2f} GB graph)" if gbytes > 129e6 else
+                          f"inputs fit L2 ({gbytes / 1e6:.0f} MB graph, not flushed: diagnostic only)"),
+                   "hits_per_step": hits / args.steps,
                    "rounds_t": rounds[-1], "graph_gen_s": d["gen_s"], "graph_ingest_s": ingest_s},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["kernel_launches"],
         "clocks": ck,

@@ -67,11 +67,16 @@ struct DBuf {  // grow-only device buffer
 // node and everything the next draw at u needs, so a walk makes one dependent DRAM access
 // per live-edge draw at equal-weight nodes (the tail's record is replicated per in-edge:
 // 32 B per edge of HBM for half the dependent latency and DRAM sectors per draw).
+// guide[e] (only when some node has unequal in-weights): for node v and bucket
+// b = floor(r * deg / in-sum) in [0, deg), guide[first(v) + b] = the live in-edge index of
+// the smallest draw of the bucket, ceil(b * in-sum / deg); the answer for any r of the
+// bucket is at or after it (Chen & Asau's guide table), usually within a step or two.
 struct Graph {
   int64_t n = 0, m = 0;
   uint4* node = nullptr;
   uint2* edge = nullptr;
   uint4* erec = nullptr;
+  uint32_t* guide = nullptr;
   int64_t* input_index = nullptr;  // CSR position -> input edge index (NULL = identity)
   int device = 0;
 };
@@ -103,7 +108,8 @@ __device__ __forceinline__ uint32_t start_node(uint64_t a, uint32_t n, uint32_t 
 __device__ __forceinline__ bool source_coin(uint32_t x1, uint32_t p32) {
   return p32 == 0xFFFFFFFFu || x1 < p32;
 }
-// Live in-edge index j in [0, deg) of a node with record nd for draw r < nd.w (in-sum).
+// Live in-edge index j in [0, deg) of a node with record nd for draw r < nd.w (in-sum):
+// the first j with r < thr[j] (equal weights: j = r / w; otherwise binary search).
 __device__ __forceinline__ uint32_t pick_in_edge(const uint2* __restrict__ edge, uint4 nd, uint32_t r) {
   if (nd.z) return r / nd.z;  // equal weights: thr[j] = (j+1) w
   uint32_t lo = 0, hi = nd.y;  // first j with r < thr[j]
@@ -113,6 +119,11 @@ __device__ __forceinline__ uint32_t pick_in_edge(const uint2* __restrict__ edge,
     if (r < t) hi = mid; else lo = mid + 1;
   }
   return lo;
+}
+
+// Guide-table bucket of draw r at a node with in-degree deg and in-sum insum (r < insum).
+__device__ __forceinline__ uint32_t guide_bucket(uint32_t r, uint32_t deg, uint32_t insum) {
+  return (uint32_t)(((uint64_t)r * deg) / insum);
 }
 
 // ------------------------------------------------------------------ primitives (primitives.cu)

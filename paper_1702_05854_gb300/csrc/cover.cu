@@ -307,6 +307,7 @@ namespace cg = cooperative_groups;
 
 struct ClusterGreedyParams {
   uint32_t U, NG, per_cta, gshift;
+  uint32_t short_walks;  // 1: walks average few elements, cover one walk per thread
   int32_t k;
   uint32_t* cnt;  // running counts | EXCLUDED
   const uint32_t* inv_off;
@@ -383,9 +384,25 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
       const uint32_t gg = u >> P.gshift;
       if (gg / per == rank) atomicOr(&dbits[(gg % per) >> 5], 1u << ((gg % per) & 31));
     }
-    // 3. cover its walks (one warp per walk): decrement every element of each newly
-    //    covered walk and mark the element's group dirty in the CTA that owns it
+    // 3. cover its walks: decrement every element of each newly covered walk and mark the
+    //    element's group dirty in the CTA that owns it (one thread per walk when walks are
+    //    short, one warp per walk otherwise)
     const uint32_t q0 = P.inv_off[u], q1 = P.inv_off[u + 1];
+    if (P.short_walks) {
+      for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
+        const uint32_t j = P.inv_walk[q];
+        if (__ldcg(&P.covered[j])) continue;
+        P.covered[j] = 1;
+        const uint32_t p1 = P.walk_eoff[j + 1];
+        for (uint32_t p = P.walk_eoff[j]; p < p1; ++p) {
+          const uint32_t x = P.entry_uidx[p];
+          atomicSub(&P.cnt[x], 1u);
+          const uint32_t gg = x >> P.gshift, gl = gg % per;
+          uint32_t* rb = cluster.map_shared_rank(dbits, gg / per);
+          atomicOr(&rb[gl >> 5], 1u << (gl & 31));
+        }
+      }
+    } else
     for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
       const uint32_t j = P.inv_walk[q];
       uint32_t fresh = 0;
@@ -525,6 +542,12 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   auto need = [](uint32_t per) { return (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64; };
   uint32_t gshift = 8, csize = 1;
   uint32_t NG = (uint32_t)(((uint64_t)U + 255) >> 8), per = NG;
+  // more CTAs (more warps to cover walks and refresh the groups they touch) for larger
+  // samples: one CTA per 2^14 walk entries
+  const uint64_t walks = (uint64_t)cv.walks;
+  const bool short_walks = walks > 0 && (uint64_t)cv.entries < 8ull * walks;
+  while ((int)csize < cluster_size && ((uint64_t)csize << 14) < (uint64_t)cv.entries) csize *= 2;
+  per = (NG + csize - 1) / csize;
   while (need(per) > smem_cap && (int)csize < cluster_size) {
     csize *= 2;
     per = (NG + csize - 1) / csize;
@@ -546,6 +569,7 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   P.NG = NG;
   P.per_cta = per;
   P.gshift = gshift;
+  P.short_walks = short_walks ? 1u : 0u;
   P.k = k;
   P.cnt = cv.cnt_work.p;
   P.inv_off = cv.inv_off.p;

@@ -162,6 +162,29 @@ __global__ void k_walk_records(const uint2* __restrict__ edge, const uint4* __re
   }
 }
 
+// Guide tables of the nodes with unequal in-weights (see Graph::guide); one warp per node.
+__global__ void k_guide(const uint4* __restrict__ node, const uint2* __restrict__ edge, int64_t n,
+                        uint32_t* __restrict__ guide, uint32_t* __restrict__ n_unequal) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t cnt = 0;
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const uint4 nd = node[v];
+    if (nd.y == 0 || nd.z != 0 || nd.w == 0) continue;  // no in-edge, equal weights, or zero in-sum
+    cnt += lane == 0 ? 1u : 0u;
+    for (uint32_t b = lane; b < nd.y; b += 32) {
+      const uint32_t lb = (uint32_t)(((uint64_t)b * nd.w + nd.y - 1) / nd.y);  // ceil(b * insum / deg)
+      uint32_t lo = 0, hi = nd.y;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (lb < edge[nd.x + mid].y) hi = mid; else lo = mid + 1;
+      }
+      guide[nd.x + b] = lo;
+    }
+  }
+  if (cnt) atomicAdd(n_unequal, cnt);
+}
+
 // ------------------------------------------------------------------ host
 static hsaw_status check_err(uint32_t* d_err, cudaStream_t s) {
   uint32_t h = 0;
@@ -191,7 +214,9 @@ static void destroy_graph(Graph& g) {
   if (g.edge) cudaFree(g.edge);
   if (g.input_index) cudaFree(g.input_index);
   if (g.erec) cudaFree(g.erec);
+  if (g.guide) cudaFree(g.guide);
   g.erec = nullptr;
+  g.guide = nullptr;
   g.node = nullptr;
   g.edge = nullptr;
   g.input_index = nullptr;
@@ -234,6 +259,19 @@ static hsaw_status finish_graph(Graph& g, uint32_t* row_start, uint32_t* d_err, 
     count_launch();
     k_walk_records<<<grid_for(g.m, 256, 1u << 16), 256, 0, s>>>(g.edge, g.node, g.m, g.erec);
     HSAW_CK(cudaGetLastError());
+    // guide tables, kept only when some node has unequal in-weights
+    HSAW_CK(cudaMalloc((void**)&g.guide, (size_t)g.m * sizeof(uint32_t)));
+    HSAW_CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
+    count_launch();
+    k_guide<<<grid_for((size_t)n * 32, 256, 1u << 20), 256, 0, s>>>(g.node, g.edge, n, g.guide, d_err);
+    HSAW_CK(cudaGetLastError());
+    uint32_t unequal = 0;
+    HSAW_CK(cudaMemcpyAsync(&unequal, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    HSAW_CK(cudaStreamSynchronize(s));
+    if (unequal == 0) {
+      cudaFree(g.guide);
+      g.guide = nullptr;
+    }
   }
   return HSAW_OK;
 }
