@@ -96,6 +96,15 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
+def reduce_over_ranks(dist, torch, device, elapsed, hits):
+    """Whole-job figures of N replicas: the slowest rank's time and the HSAWs of all ranks."""
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    h = torch.tensor([float(hits)], dtype=torch.float64, device=device)
+    dist.all_reduce(h)
+    return float(t.item()), float(h.item())
+
+
 def make_workload(scale, which="c3"):
     """c3: the billion-edge eSI stop-rule solve (default); c2: the nSI R-MAT 20 random-LT
     solve with N = 10 M HSAWs; c1: the eSI Chung-Lu 16 K solve with N = 200 K."""
@@ -399,12 +408,7 @@ def main():
     hs.hsaw_profile_enable(False)
     ck = clocks.stop()
     if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        h = torch.tensor([hits], dtype=torch.float64, device="cuda")
-        dist.all_reduce(h)
-        hits_all = float(h.item())
+        elapsed, hits_all = reduce_over_ranks(dist, torch, "cuda", elapsed, hits)
     else:
         hits_all = float(hits)
     value = hits_all / elapsed

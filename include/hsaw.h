@@ -91,6 +91,12 @@ HSAW_API hsaw_status hsaw_graph_info(hsaw_graph g, int64_t* n, int64_t* m);
 HSAW_API hsaw_status hsaw_graph_export(hsaw_graph g, int64_t* in_row_ptr, int32_t* in_src, int32_t* in_dst,
                               uint32_t* thr, int64_t* input_index, void* stream);
 
+/* Endpoints of edge `edge_id` (a CSR position): *src -> *dst, and its index in the input
+ * edge list (the position itself for hsaw_graph_from_csr).  Any output may be NULL.
+ * HSAW_E_RANGE when edge_id is outside [0, m). */
+HSAW_API hsaw_status hsaw_graph_edge(hsaw_graph g, int64_t edge_id, int32_t* src, int32_t* dst,
+                                     int64_t* input_index);
+
 /* ------------------------------------------------------------------ query
  * Sec. 2.2: suspects V_I = (V_I, p) (Eq. "prob_src_set"), candidates C, budget k
  * (Defs. "edge_remove" / "node_remove"); Alg. 6 inputs eps, delta. */
@@ -132,6 +138,20 @@ typedef struct {
  * are taken, so exactly k ids are returned.  Errors: HSAW_E_INVALID, HSAW_E_RANGE,
  * HSAW_E_NOMEM, HSAW_E_DEVICE, HSAW_E_STEP_CAP, HSAW_E_TIMEOUT. */
 HSAW_API hsaw_status hsaw_solve(hsaw_graph g, const hsaw_query* q, hsaw_result* r, void* stream);
+
+/* Spread of V_I on the residual graph G' (Eq. "sus_nod": the removed edges, or nodes,
+ * deleted), by HSAW sampling: draws q->n_hsaw hits on G' (attempts from 0, q's seed and
+ * suspects) and returns *spread = n hits / attempts, the unbiased estimate of I_G'(V_I)
+ * (Thm. "rr_edge" with T = E), and *std_err = n sqrt(f (1 - f) / attempts), f = hits /
+ * attempts.  removed: edge ids (q->mode == HSAW_EDGE) or node ids (HSAW_NODE), host
+ * array, may be NULL when n_removed == 0.  D_hat(T) = spread(no removal) - spread(T). */
+HSAW_API hsaw_status hsaw_estimate_spread(hsaw_graph g, const hsaw_query* q, const int64_t* removed,
+                                          int32_t n_removed, double* spread, double* std_err, void* stream);
+
+/* Test hook (fault injection on the host): the n-th device allocation made by the library
+ * from now on fails as if the device were out of memory (n >= 1); n <= 0 disables.  The
+ * failing call returns HSAW_E_NOMEM and leaves the library usable. */
+HSAW_API hsaw_status hsaw_debug_fail_alloc_after(int64_t n);
 
 /* ------------------------------------------------------------------ batched and served solves
  * Not in the paper: many interdiction instances at once (batching) and a request loop

@@ -72,6 +72,10 @@ SIGNATURES = {
     "hsaw_check": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, _dbl, _dbl, ctypes.POINTER(_dbl)]),
     "hsaw_sample_hits_static": (ctypes.c_int, [_p, _p, _u64, _u64, _i64, _p, _p, _i64, ctypes.POINTER(_i64), _p]),
     "hsaw_solve_batch": (ctypes.c_int, [_p, _p, _p, _p, _i32, _i32, _p]),
+    "hsaw_graph_edge": (ctypes.c_int, [_p, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "hsaw_estimate_spread": (ctypes.c_int, [_p, ctypes.POINTER(hsaw_query), _p, _i32, ctypes.POINTER(_dbl),
+                                            ctypes.POINTER(_dbl), _p]),
+    "hsaw_debug_fail_alloc_after": (ctypes.c_int, [_i64]),
     "hsaw_server_create": (ctypes.c_int, [_p, _i32, ctypes.c_size_t, _i32, ctypes.POINTER(_p)]),
     "hsaw_server_submit": (ctypes.c_int, [_p, _i32, ctypes.POINTER(hsaw_query), ctypes.POINTER(_u64)]),
     "hsaw_server_poll": (ctypes.c_int, [_p, _u64, ctypes.POINTER(hsaw_result), _i32, ctypes.POINTER(_dbl)]),
@@ -182,6 +186,28 @@ class Graph:
         ii = np.empty(self.m, np.int64)
         _check(load().hsaw_graph_export(self._h, _ptr(rp), _ptr(s), _ptr(d), _ptr(t), _ptr(ii), _stream(stream)))
         return rp, s, d, t, ii
+
+
+def hsaw_graph_edge(graph, edge_id: int):
+    """(src, dst, input_index) of a CSR edge id."""
+    a, b, c = _i32(), _i32(), _i64()
+    _check(load().hsaw_graph_edge(graph.handle, edge_id, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def hsaw_estimate_spread(graph, query, removed=None, stream=None):
+    """(spread, std_err) of V_I on the graph with `removed` edges (eSI) or nodes (nSI)."""
+    rem = np.ascontiguousarray(removed if removed is not None else np.zeros(0), np.int64)
+    q = query.c()
+    sp, se = _dbl(), _dbl()
+    _check(load().hsaw_estimate_spread(graph.handle, ctypes.byref(q), _ptr(rem) if rem.size else None, rem.size,
+                                       ctypes.byref(sp), ctypes.byref(se), _stream(stream)))
+    return sp.value, se.value
+
+
+def hsaw_debug_fail_alloc_after(n: int):
+    """Test hook: make the n-th device allocation from now on fail (n <= 0 disables)."""
+    _check(load().hsaw_debug_fail_alloc_after(n))
 
 
 def hsaw_graph_from_edges(n, src, dst, w_fixed, stream=None) -> Graph:

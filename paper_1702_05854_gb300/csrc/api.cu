@@ -231,6 +231,46 @@ hsaw_status hsaw_sample(hsaw_graph g, const hsaw_query* q, uint64_t first_attemp
   return HSAW_OK;
 }
 
+__global__ void k_mark_removed(const int64_t* __restrict__ ids, int32_t cnt, uint8_t* __restrict__ mask) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) mask[ids[i]] = 1;
+}
+
+hsaw_status hsaw_estimate_spread(hsaw_graph g, const hsaw_query* q, const int64_t* removed, int32_t n_removed,
+                                 double* spread, double* std_err, void* stream) {
+  if (!g || !q || !spread || (n_removed > 0 && !removed)) return fail(HSAW_E_INVALID, "estimate: NULL argument");
+  if (q->n_hsaw < 1) return fail(HSAW_E_INVALID, "estimate: n_hsaw < 1");
+  const Graph& G = g->g;
+  const bool edges = q->mode == HSAW_EDGE;
+  const int64_t M = edges ? G.m : G.n;
+  for (int32_t i = 0; i < n_removed; ++i)
+    if (removed[i] < 0 || removed[i] >= M) return fail(HSAW_E_RANGE, "estimate: removed id out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  SolveScratch W(s);
+  HSAW_TRY(query_upload(G, q, W.qd, s));
+  if (n_removed > 0) {
+    uint8_t* mask = nullptr;
+    int64_t* d_ids = nullptr;
+    HSAW_TRY(dmalloc((void**)&mask, (size_t)M, s));
+    (edges ? W.qd.edge_removed : W.qd.node_removed) = mask;
+    W.qd.owns_removed = true;
+    HSAW_CK(cudaMemsetAsync(mask, 0, (size_t)M, s));
+    HSAW_TRY(dmalloc((void**)&d_ids, (size_t)n_removed * 8, s));
+    HSAW_CK(cudaMemcpyAsync(d_ids, removed, (size_t)n_removed * 8, cudaMemcpyHostToDevice, s));
+    count_launch();
+    k_mark_removed<<<grid_for(n_removed, 256, 1024), 256, 0, s>>>(d_ids, n_removed, mask);
+    HSAW_CK(cudaGetLastError());
+    dfree(d_ids, s);
+  }
+  HSAW_TRY(stream_init(W.st, 0, q->max_attempts, s));
+  HSAW_TRY(stream_extend(G, W.qd, W.st, q->n_hsaw, s));
+  uint64_t last = 0;
+  HSAW_TRY(aid_at(W.st, q->n_hsaw - 1, &last, s));
+  const double A = (double)(last + 1), f = (double)q->n_hsaw / A, n = (double)G.n;
+  *spread = n * (double)q->n_hsaw / A;
+  if (std_err) *std_err = n * std::sqrt(f * (1.0 - f) / A);
+  return HSAW_OK;
+}
+
 hsaw_status hsaw_walks_info(hsaw_walks w, int64_t* count, int64_t* total_nodes, uint64_t* attempts, uint64_t* steps) {
   if (!w) return fail(HSAW_E_INVALID, "walks: NULL handle");
   if (count) *count = w->st.count;

@@ -2,6 +2,7 @@
 // in-weight sums, per-node records and validation of the LT in-weight condition.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -27,7 +28,13 @@ hsaw_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
 }
 
 static std::once_flag g_pool_once;
+static std::atomic<long long> g_fail_countdown{0};  // test hook: > 0 counts down to a failing allocation
 hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
+  if (g_fail_countdown.load(std::memory_order_relaxed) > 0 && g_fail_countdown.fetch_sub(1) == 1) {
+    *p = nullptr;
+    t_err = "device allocation failed (injected by hsaw_debug_fail_alloc_after)";
+    return HSAW_E_NOMEM;
+  }
   std::call_once(g_pool_once, [] {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -440,6 +447,45 @@ hsaw_status hsaw_graph_destroy(hsaw_graph g) {
   cudaDeviceSynchronize();
   destroy_graph(g->g);
   delete g;
+  return HSAW_OK;
+}
+
+hsaw_status hsaw_debug_fail_alloc_after(int64_t n) {
+  g_fail_countdown.store(n > 0 ? n : 0);
+  return HSAW_OK;
+}
+
+hsaw_status hsaw_graph_edge(hsaw_graph g, int64_t edge_id, int32_t* src, int32_t* dst, int64_t* input_index) {
+  if (!g) return fail(HSAW_E_INVALID, "graph: NULL handle");
+  if (edge_id < 0 || edge_id >= g->g.m) return fail(HSAW_E_RANGE, "graph: edge id outside [0, m)");
+  uint2 ed;
+  HSAW_CK(cudaMemcpy(&ed, g->g.edge + edge_id, sizeof(uint2), cudaMemcpyDeviceToHost));
+  if (src) *src = (int32_t)ed.x;
+  if (dst) {  // the node whose in-range holds edge_id: binary search over the node records
+    int64_t lo = 0, hi = g->g.n - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) / 2;
+      uint4 nd;
+      HSAW_CK(cudaMemcpy(&nd, g->g.node + mid, sizeof(uint4), cudaMemcpyDeviceToHost));
+      if ((int64_t)nd.x <= edge_id) lo = mid; else hi = mid - 1;
+    }
+    // nodes without in-edges share their first position with the next node: take the
+    // last node starting at or before edge_id whose range is non-empty
+    uint4 nd;
+    HSAW_CK(cudaMemcpy(&nd, g->g.node + lo, sizeof(uint4), cudaMemcpyDeviceToHost));
+    while (lo > 0 && (int64_t)nd.x + nd.y <= edge_id) {
+      --lo;
+      HSAW_CK(cudaMemcpy(&nd, g->g.node + lo, sizeof(uint4), cudaMemcpyDeviceToHost));
+    }
+    *dst = (int32_t)lo;
+  }
+  if (input_index) {
+    if (g->g.input_index) {
+      HSAW_CK(cudaMemcpy(input_index, g->g.input_index + edge_id, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    } else {
+      *input_index = edge_id;
+    }
+  }
   return HSAW_OK;
 }
 
