@@ -329,6 +329,45 @@ def run_serve_mode(args, hs, torch):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep_mode(args, hs, torch):
+    """Scalability sweep in the shape of the paper's Fig. "scale": R-MAT graphs with n = 2^13
+    .. 2^27 nodes and m/n in {5, 10, 15}; nSI stop-rule solves with the paper's experimental
+    query: 1,000 random suspects with random probabilities p, k = 100, eps = 0.1,
+    delta = 1/n (Sec. 6 "Parameter Settings")."""
+    scales = [int(x) for x in args.sweep_scales.split(",")]
+    dens = [int(x) for x in args.sweep_density.split(",")]
+    rows = []
+    for sc in scales:
+        for dn in dens:
+            n = 1 << sc
+            t0 = time.time()
+            src, dst = synth.rmat_graph(sc, dn, seed=synth.SEED_GRAPH)
+            w = synth.wc_weights(n, dst)
+            S = synth.sources(n, min(1000, n), seed=synth.SEED_SOURCES)
+            p = synth.probabilities(S.shape[0], seed=synth.SEED_SOURCES)
+            gen_s = time.time() - t0
+            g = hs.hsaw_graph_from_edges(n, src, dst, w)
+            del src, dst, w
+            q = hs.Query(sources=S, p_fixed=p, mode=hs.HSAW_NODE, k=100, sampling=hs.HSAW_STOP_RULE, eps=0.1,
+                         seed=synth.SEED_WALKS)
+            hs.hsaw_solve(g, q)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ids, gains, r = hs.hsaw_solve(g, q)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            rows.append({"n": n, "m": dn * n, "solve_s": dt, "hsaws": r["hits"], "rounds_t": r["rounds_t"],
+                         "hsaws_per_s": r["hits"] / dt, "gen_s": gen_s})
+            g.close()
+            print(json.dumps({"sweep_point": rows[-1]}), file=sys.stderr, flush=True)
+    line = {"metric": "nSI solve time vs graph size (R-MAT, 1000 suspects with random p, k = 100)",
+            "value": rows[-1]["solve_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": rows[-1]["solve_s"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "sweep", "scales": scales, "density": dens}, "points": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,7 +379,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-attempts", type=int, default=50_000)
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "sweep"])
+    ap.add_argument("--sweep-scales", default="13,17,20,23,27")
+    ap.add_argument("--sweep-density", default="5,10,15")
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-nmax", type=float, default=1e6)
@@ -367,6 +408,8 @@ def main():
         return run_batch_mode(args, hs, torch)
     if args.mode == "serve":
         return run_serve_mode(args, hs, torch)
+    if args.mode == "sweep":
+        return run_sweep_mode(args, hs, torch)
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -1,8 +1,8 @@
 // HSAW sampling (Sec. 4, Alg. 1-3) on sm_103a.
 //
 // Attempt a is one live-edge world: node v's live in-edge and source coin come from
-// Philox(seed; a, v), so a walk is a trajectory of a functional graph and Brent's cycle
-// detection (Sec. 4.2.2) is exact in O(1) space per walk.  A persistent warp claims
+// Philox(seed; a, v), so a walk is a trajectory of a functional graph and O(1)-space cycle
+// detection (the idea of Sec. 4.2.2) is exact: any revisit proves the cycle.  A persistent warp claims
 // chunks of consecutive attempts; lanes that finish take the next attempt of the warp's
 // chunk cursor at once (no lane waits for the warp's longest walk).  Hits are recorded
 // per chunk as (attempt offset, length); the compaction kernel orders each chunk's hits
@@ -246,7 +246,9 @@ __global__ void k_classify(SampleParams P, uint64_t first, int64_t count, int8_t
                            int32_t* __restrict__ length) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t a = first + (uint64_t)i;
-    uint32_t v = start_node(a, P.n, P.k0, P.k1), tort = v, power = 1, lam = 0, len = 1;
+    uint32_t v = start_node(a, P.n, P.k0, P.k1), len = 1;
+    Ckpt ck;
+    ck.reset(v);
     int out = -1;
     if (HAS_REM && P.node_removed && P.node_removed[v]) out = 3;
     while (out < 0) {
@@ -258,8 +260,8 @@ __global__ void k_classify(SampleParams P, uint64_t first, int64_t count, int8_t
       const uint32_t e = nd.x + pick_in_edge(P.edge, nd, x.x);
       const uint32_t u = __ldg(&P.edge[e].x);
       if (HAS_REM && ((P.edge_removed && P.edge_removed[e]) || (P.node_removed && P.node_removed[u]))) { out = 3; break; }
-      if (u == tort) { out = 2; break; }
-      if (++lam == power) { tort = u; power <<= 1; lam = 0; }
+      if (ck.seen(u)) { out = 2; break; }
+      ck.keep(u, len);
       v = u;
       if (++len > P.step_cap) { atomicOr(P.chunk_ctr + 1, ST_STEP_CAP); out = 0; break; }
     }
