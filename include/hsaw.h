@@ -97,6 +97,19 @@ HSAW_API hsaw_status hsaw_graph_export(hsaw_graph g, int64_t* in_row_ptr, int32_
 HSAW_API hsaw_status hsaw_graph_edge(hsaw_graph g, int64_t edge_id, int32_t* src, int32_t* dst,
                                      int64_t* input_index);
 
+/* Walk pool (not in the paper; serving many queries on one graph).  Attempt a's walk
+ * ignoring sources - its nodes until no live in-edge or a cycle - does not depend on the
+ * query: a query's HSAW of attempt a is that trace's prefix up to its first real source
+ * (same node-keyed draws and coins).  hsaw_graph_build_walk_pool stores the traces of
+ * attempts [0, attempts) for walk seed `seed` on the device (about 8 B per trace node);
+ * afterwards every solve, sample or served query on g with q->seed == seed and no removed
+ * elements scans these traces for its attempts below `attempts` instead of walking them,
+ * and samples the rest as usual, with bit-identical results.  Building replaces any
+ * previous pool; do not build or drop while other calls use g.  HSAW_E_NOMEM if the
+ * traces do not fit.  hsaw_graph_drop_walk_pool frees it. */
+HSAW_API hsaw_status hsaw_graph_build_walk_pool(hsaw_graph g, uint64_t seed, uint64_t attempts, void* stream);
+HSAW_API hsaw_status hsaw_graph_drop_walk_pool(hsaw_graph g);
+
 /* ------------------------------------------------------------------ query
  * Sec. 2.2: suspects V_I = (V_I, p) (Eq. "prob_src_set"), candidates C, budget k
  * (Defs. "edge_remove" / "node_remove"); Alg. 6 inputs eps, delta. */

@@ -76,6 +76,8 @@ SIGNATURES = {
     "hsaw_estimate_spread": (ctypes.c_int, [_p, ctypes.POINTER(hsaw_query), _p, _i32, ctypes.POINTER(_dbl),
                                             ctypes.POINTER(_dbl), _p]),
     "hsaw_debug_fail_alloc_after": (ctypes.c_int, [_i64]),
+    "hsaw_graph_build_walk_pool": (ctypes.c_int, [_p, _u64, _u64, _p]),
+    "hsaw_graph_drop_walk_pool": (ctypes.c_int, [_p]),
     "hsaw_server_create": (ctypes.c_int, [_p, _i32, ctypes.c_size_t, _i32, ctypes.POINTER(_p)]),
     "hsaw_server_submit": (ctypes.c_int, [_p, _i32, ctypes.POINTER(hsaw_query), ctypes.POINTER(_u64)]),
     "hsaw_server_poll": (ctypes.c_int, [_p, _u64, ctypes.POINTER(hsaw_result), _i32, ctypes.POINTER(_dbl)]),
@@ -176,6 +178,13 @@ class Graph:
     @property
     def handle(self):
         return self._h
+
+    def build_walk_pool(self, seed: int, attempts: int, stream=None):
+        """Keep the query-independent traces of attempts [0, attempts) for walk seed `seed`."""
+        _check(load().hsaw_graph_build_walk_pool(self._h, seed, attempts, _stream(stream)))
+
+    def drop_walk_pool(self):
+        _check(load().hsaw_graph_drop_walk_pool(self._h))
 
     def export(self, stream=None):
         """Host copy of the device CSR: (row_ptr, src, dst, thr, input_index)."""

@@ -71,8 +71,22 @@ struct DBuf {  // grow-only device buffer
 // b = floor(r * deg / in-sum) in [0, deg), guide[first(v) + b] = the live in-edge index of
 // the smallest draw of the bucket, ceil(b * in-sum / deg); the answer for any r of the
 // bucket is at or after it (Chen & Asau's guide table), usually within a step or two.
+// Walk pool (query-independent traces): for walk seed `seed`, trace a (a < attempts) is
+// attempt a's walk ignoring sources - its nodes until no live in-edge or a detected cycle
+// (nodes[off[a] .. off[a+1]), edges from off[a] - a).  A query's HSAW of attempt a is the
+// trace's prefix up to its first real source (the source test is per node, with the same
+// node-keyed coin), so queries with this seed scan traces instead of re-walking.
+struct WalkPool {
+  uint64_t seed = 0;
+  uint64_t attempts = 0;
+  uint64_t* off = nullptr;
+  int32_t* nodes = nullptr;
+  int32_t* edges = nullptr;
+};
+
 struct Graph {
   int64_t n = 0, m = 0;
+  WalkPool pool;
   uint4* node = nullptr;
   uint2* edge = nullptr;
   uint4* erec = nullptr;
@@ -125,6 +139,33 @@ __device__ __forceinline__ uint32_t pick_in_edge(const uint2* __restrict__ edge,
 __device__ __forceinline__ uint32_t guide_bucket(uint32_t r, uint32_t deg, uint32_t insum) {
   return (uint32_t)(((uint64_t)r * deg) / insum);
 }
+
+// Exact cycle detection in registers: the walk keeps the nodes it saw at positions
+// 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 18, ... (each 1.25x the last) in a ring of 8
+// registers.  A tail node equal to a kept node is a revisit, so the world's backward chain
+// is a cycle (miss); a cycle entered at position mu is seen within about 0.25 mu + lambda
+// draws, against mu + lambda for a whole-walk check and about 2 (mu + lambda) for Brent.
+struct Ckpt {
+  uint32_t c0, c1, c2, c3, c4, c5, c6, c7;
+  uint32_t count, next;
+  __device__ __forceinline__ void reset(uint32_t v) {
+    c0 = c1 = c2 = c3 = c4 = c5 = c6 = c7 = v;
+    count = 1;
+    next = 1;
+  }
+  __device__ __forceinline__ bool seen(uint32_t u) const {
+    return (u == c0) | (u == c1) | (u == c2) | (u == c3) | (u == c4) | (u == c5) | (u == c6) | (u == c7);
+  }
+  // u is the node at walk position pos (>= 1)
+  __device__ __forceinline__ void keep(uint32_t u, uint32_t pos) {
+    if (pos < next) return;
+    const uint32_t slot = count & 7u;
+    c0 = slot == 0 ? u : c0; c1 = slot == 1 ? u : c1; c2 = slot == 2 ? u : c2; c3 = slot == 3 ? u : c3;
+    c4 = slot == 4 ? u : c4; c5 = slot == 5 ? u : c5; c6 = slot == 6 ? u : c6; c7 = slot == 7 ? u : c7;
+    ++count;
+    next = next + max(1u, next >> 2);
+  }
+};
 
 // ------------------------------------------------------------------ primitives (primitives.cu)
 // Exclusive prefix sum in place; *total (device, may be NULL) receives the sum.

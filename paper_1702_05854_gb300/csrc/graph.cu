@@ -216,7 +216,10 @@ static hsaw_status stage(const T* p, size_t count, bool on_device, cudaStream_t 
   return HSAW_OK;
 }
 
+void pool_release(WalkPool& p);
+
 static void destroy_graph(Graph& g) {
+  pool_release(g.pool);
   if (g.node) cudaFree(g.node);
   if (g.edge) cudaFree(g.edge);
   if (g.input_index) cudaFree(g.input_index);

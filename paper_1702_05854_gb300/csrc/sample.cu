@@ -46,33 +46,6 @@ struct SampleParams {
   unsigned long long* steps;
 };
 
-// Exact cycle detection in registers: the walk keeps the nodes it saw at positions
-// 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 18, ... (each 1.25x the last) in a ring of 8
-// registers.  A tail node equal to a kept node is a revisit, so the world's backward chain
-// is a cycle (miss); a cycle entered at position mu is seen within about 0.25 mu + lambda
-// draws, against mu + lambda for a whole-walk check and about 2 (mu + lambda) for Brent.
-struct Ckpt {
-  uint32_t c0, c1, c2, c3, c4, c5, c6, c7;
-  uint32_t count, next;
-  __device__ __forceinline__ void reset(uint32_t v) {
-    c0 = c1 = c2 = c3 = c4 = c5 = c6 = c7 = v;
-    count = 1;
-    next = 1;
-  }
-  __device__ __forceinline__ bool seen(uint32_t u) const {
-    return (u == c0) | (u == c1) | (u == c2) | (u == c3) | (u == c4) | (u == c5) | (u == c6) | (u == c7);
-  }
-  // u is the node at walk position pos (>= 1)
-  __device__ __forceinline__ void keep(uint32_t u, uint32_t pos) {
-    if (pos < next) return;
-    const uint32_t slot = count & 7u;
-    c0 = slot == 0 ? u : c0; c1 = slot == 1 ? u : c1; c2 = slot == 2 ? u : c2; c3 = slot == 3 ? u : c3;
-    c4 = slot == 4 ? u : c4; c5 = slot == 5 ? u : c5; c6 = slot == 6 ? u : c6; c7 = slot == 7 ? u : c7;
-    ++count;
-    next = next + max(1u, next >> 2);
-  }
-};
-
 template <bool HAS_P, bool HAS_REM>
 __global__ void __launch_bounds__(256, 6) k_sample(SampleParams P) {
   const unsigned FULL = 0xffffffffu;
@@ -381,6 +354,9 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
   const uint32_t CHUNK = 256;
   unsigned long long* d_steps = nullptr;
   HSAW_TRY(st.tmp64.ensure(1, s));
+  // traces of the walk pool serve this query's attempts below pool.attempts when the walk
+  // seed matches and the graph is not a residual one
+  const bool pool_ok = g.pool.nodes && g.pool.seed == qd.seed && !qd.edge_removed && !qd.node_removed;
   while (st.count < want) {
     if (cancel_requested()) return fail(HSAW_E_CANCELLED, "sampling: query cancelled");
     const uint64_t used = st.next_attempt - st.first_attempt;
@@ -394,7 +370,9 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
     uint64_t batch = (uint64_t)target;
     batch = std::min<uint64_t>(batch, st.max_attempts - used);
     batch = (batch + CHUNK - 1) / CHUNK * CHUNK;
-    const uint32_t n_chunks = (uint32_t)(batch / CHUNK);
+    const bool pooled = pool_ok && st.next_attempt < g.pool.attempts;
+    if (pooled) batch = std::min<uint64_t>(batch, g.pool.attempts - st.next_attempt);  // scans stop at the pool's end
+    const uint32_t n_chunks = (uint32_t)((batch + CHUNK - 1) / CHUNK);
     // records per chunk: a few standard deviations above the expected hits, else all
     double exp_hits = std::max(st.hit_rate, 0.0) * CHUNK;
     uint32_t cap = (uint32_t)std::min<double>(CHUNK, std::ceil(exp_hits + 6.0 * std::sqrt(exp_hits + 1.0) + 8.0));
@@ -418,9 +396,13 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
       P.steps = d_steps;
       const unsigned grid = (unsigned)std::max(1, std::min<int>(sm_count() * sample_blocks_per_sm(),
                                                                  (int)((n_chunks + 7) / 8)));
-      void* prof = profile_begin(s);
-      launch_sample(P, grid, s);
-      profile_end(prof, s, batch);
+      if (pooled) {
+        pool_scan_launch(g, qd, P.a0, P.n_attempts, CHUNK, cap, st.chunk_hits.p, st.recs.p, st.ctrs.p + 3, s);
+      } else {
+        void* prof = profile_begin(s);
+        launch_sample(P, grid, s);
+        profile_end(prof, s, batch);
+      }
       HSAW_CK(cudaGetLastError());
       count_launch();
       k_clamp<<<grid_for(n_chunks, 256, 4096), 256, 0, s>>>(st.chunk_hits.p, st.chunk_off.p, n_chunks, cap);
@@ -432,7 +414,7 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
       HSAW_CK(cudaMemcpyAsync(&hs, d_steps, 8, cudaMemcpyDeviceToHost, s));
       HSAW_CK(cudaStreamSynchronize(s));
       if (h[1] & ST_STEP_CAP) return fail(HSAW_E_STEP_CAP, "sampling: a walk exceeded its step guard");
-      if ((h[1] & ST_OVERFLOW) && cap < CHUNK) {
+      if (((h[1] & ST_OVERFLOW) || h[3]) && cap < CHUNK) {
         cap = CHUNK;  // rare: rerun this launch with room for every attempt to hit
         continue;
       }
@@ -464,10 +446,14 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
         const int64_t tot = st.total_nodes + (int64_t)added;
         HSAW_TRY(st.nodes.ensure((size_t)tot, s, true));
         HSAW_TRY(st.edges.ensure((size_t)tot, s, true));
-        count_launch();
-        k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, P.k0, P.k1, st.aid.p,
-                                                                     st.len.p, st.node_off.p, st.count,
-                                                                     st.count + new_hits, st.nodes.p, st.edges.p);
+        if (pooled) {
+          pool_copy_launch(g, st, st.count, st.count + new_hits, s);
+        } else {
+          count_launch();
+          k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, P.k0, P.k1,
+                                                                       st.aid.p, st.len.p, st.node_off.p, st.count,
+                                                                       st.count + new_hits, st.nodes.p, st.edges.p);
+        }
         HSAW_CK(cudaGetLastError());
         st.total_nodes = tot;
         st.count += new_hits;

@@ -73,6 +73,13 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
 hsaw_status cover_count(const Stream& st, hsaw_mode mode, int64_t first, int64_t count, const int64_t* T, int32_t k,
                         uint64_t* cov, cudaStream_t s);
 
+// Walk pool (pool.cu).
+void pool_release(WalkPool& p);
+hsaw_status pool_build(Graph& g, uint64_t seed, uint64_t attempts, cudaStream_t s);
+void pool_scan_launch(const Graph& g, const QueryDev& qd, uint64_t a0, uint32_t n_attempts, uint32_t chunk,
+                      uint32_t cap, uint32_t* chunk_hits, uint2* recs, uint32_t* status, cudaStream_t s);
+void pool_copy_launch(const Graph& g, const Stream& st, int64_t h0, int64_t h1, cudaStream_t s);
+
 // Cancellation of the calling thread's current solve (set by the server's workers):
 // checked between sampler launches and between stopping-rule rounds.
 void set_cancel_flag(const volatile int* flag);

@@ -1,0 +1,88 @@
+"""Walk-pool reuse gives exactly the plain solver's results (GPU).
+
+A pool keeps attempt traces that do not depend on the query; queries with the pool's walk
+seed scan them for attempts inside the pool and sample the rest.  Every result here is
+compared with the same call on a graph without a pool.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+hs = pytest.importorskip("paper_1702_05854_gb300")
+
+
+def pair(d):
+    plain = hs.hsaw_graph_from_edges(d["n"], d["src"], d["dst"], d["w"])
+    pooled = hs.hsaw_graph_from_edges(d["n"], d["src"], d["dst"], d["w"])
+    return plain, pooled
+
+
+@pytest.fixture(scope="module")
+def c1():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = synth.workload_c1()
+    plain, pooled = pair(d)
+    pooled.build_walk_pool(seed=4, attempts=1 << 22)
+    return d, plain, pooled
+
+
+def same_prefix(a, b, n):
+    """The first n walks of two exported streams (they may hold different overshoots)."""
+    (aa, oa, na, ea), (ab, ob, nb, eb) = a, b
+    assert np.array_equal(aa[:n], ab[:n]) and np.array_equal(oa[:n + 1], ob[:n + 1])
+    assert np.array_equal(na[:oa[n]], nb[:ob[n]]) and np.array_equal(ea[:oa[n] - n], eb[:ob[n] - n])
+
+
+def same_solve(a, b):
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for f in ("rounds_t", "hits", "attempts", "cov_R", "cov_Rprime", "hits_Rprime", "attempts_Rprime",
+              "spread_base_est", "spread_reduction_est"):
+        assert a[2][f] == b[2][f], f
+
+
+@pytest.mark.parametrize("mode", [hs.HSAW_EDGE, hs.HSAW_NODE])
+def test_pooled_solves_match_plain(c1, mode):
+    d, plain, pooled = c1
+    p = synth.probabilities(len(d["sources"]))
+    queries = [hs.Query(sources=d["sources"], mode=mode, k=10, n_hsaw=20_000, seed=4),
+               hs.Query(sources=d["sources"], mode=mode, k=10, sampling=hs.HSAW_STOP_RULE, eps=0.1, seed=4),
+               hs.Query(sources=d["sources"], p_fixed=p, mode=mode, k=20, n_hsaw=8_000, seed=4),
+               # needs attempts beyond the pool's 2^22: scans then samples
+               hs.Query(sources=d["sources"][:2], mode=mode, k=5, n_hsaw=5_000, seed=4),
+               hs.Query(sources=d["sources"], mode=mode, k=10, n_hsaw=5_000, seed=5)]  # other seed: no pool
+    for q in queries:
+        same_solve(hs.hsaw_solve(pooled, q), hs.hsaw_solve(plain, q))
+
+
+def test_pooled_streams_match_plain(c1):
+    d, plain, pooled = c1
+    q = hs.Query(sources=d["sources"], k=1, seed=4)
+    for first in (0, 12345, (1 << 22) - 3000):
+        same_prefix(hs.hsaw_sample(pooled, q, first, 3000).export(), hs.hsaw_sample(plain, q, first, 3000).export(),
+                    3000)
+    # residual graphs bypass the pool and still agree
+    er = (np.arange(d["m"]) % 7 == 0).astype(np.uint8)
+    same_prefix(hs.hsaw_sample(pooled, q, 0, 2000, edge_removed=er).export(),
+                hs.hsaw_sample(plain, q, 0, 2000, edge_removed=er).export(), 2000)
+
+
+def test_pooled_unequal_weights_and_served(c1):
+    d = synth.workload_rmat(14, "random", 50, 20, "node")
+    plain, pooled = pair(d)
+    pooled.build_walk_pool(seed=7, attempts=1 << 21)
+    q = hs.Query(sources=d["sources"], mode=hs.HSAW_NODE, k=20, sampling=hs.HSAW_STOP_RULE, eps=0.2, seed=7)
+    same_solve(hs.hsaw_solve(pooled, q), hs.hsaw_solve(plain, q))
+    srv = hs.Server([pooled], workers=4)
+    ts = [srv.submit(0, q) for _ in range(6)]
+    ref = hs.hsaw_solve(plain, q)
+    for t in ts:
+        ids, gains, r, lat = srv.poll(t)
+        same_solve((ids, gains, r), ref)
+    srv.close()
+    pooled.drop_walk_pool()
+    same_solve(hs.hsaw_solve(pooled, q), ref)
