@@ -177,8 +177,11 @@ def run_reference(args, rank, world):
 
 
 def same_result(a, b):
-    """Equal result counters and estimates (NaN equal to NaN)."""
+    """Equal result counters and estimates (NaN equal to NaN); `steps` counts the draws a
+    solve executed (none for attempts served from a walk pool), not part of the result."""
     for key in a:
+        if key == "steps":
+            continue
         x, y = a[key], b[key]
         if isinstance(x, float) and x != x:
             if y == y:
@@ -281,6 +284,10 @@ def run_serve_mode(args, hs, torch):
         graphs.append(hs.hsaw_graph_from_edges(n, src, dst, synth.wc_weights(n, dst)))
         gm.append((n, int(src.shape[0])))
     qs = serve_queries(args.serve_queries, gm, args.serve_min_sources)
+    pool_attempts = int(args.serve_pool_attempts)
+    if pool_attempts:  # every query on a graph shares its walk seed, so traces can be reused
+        for _, kw in qs:
+            kw["seed"] = synth.SEED_WALKS
     queries = [(gi, hs.Query(**kw)) for gi, kw in qs]
     # serial: one query at a time on the same stream of queries
     hs.hsaw_solve(graphs[queries[0][0]], queries[0][1])
@@ -288,11 +295,20 @@ def run_serve_mode(args, hs, torch):
     alone = [hs.hsaw_solve(graphs[gi], q) for gi, q in queries]
     t_serial = time.perf_counter() - t0
     serial_rate = len(queries) / t_serial
+    pool_s = 0.0
+    if pool_attempts:
+        t0 = time.perf_counter()
+        for g in graphs:
+            g.build_walk_pool(synth.SEED_WALKS, pool_attempts)
+        torch.cuda.synchronize()
+        pool_s = time.perf_counter() - t0
+        hs.hsaw_solve(graphs[queries[0][0]], queries[0][1])
     rates = [float(x) for x in args.serve_rates.split(",")]
     per_rate = []
     identical = True
     clocks = Clocks(0)
     clocks.start()
+    hs.hsaw_profile_enable(True)
     for rate in rates:
         srv = hs.Server(graphs, workers=args.serve_workers)
         rng = np.random.default_rng(int(rate))
@@ -316,6 +332,8 @@ def run_serve_mode(args, hs, torch):
         per_rate.append({"offered_qps": rate, "solves_per_s": len(queries) / (t_end - t_start),
                          "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99))})
     ck = clocks.stop()
+    prof = hs.hsaw_profile_read()
+    hs.hsaw_profile_enable(False)
     best = max(per_rate, key=lambda x: x["solves_per_s"])
     line = {"metric": "served SI solves/s and p50/p99 latency (Poisson arrivals)", "value": best["solves_per_s"],
             "unit": "solves/s", "n_gpus": 1, "steps": len(rates), "warmup": 1,
@@ -323,9 +341,12 @@ def run_serve_mode(args, hs, torch):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "serving", "graphs": [f"rmat{sc}-wc" for sc in scales],
                        "queries_per_rate": len(queries), "sources": [args.serve_min_sources, 1000], "k": [10, 1000],
-                       "eps": [0.1, 0.2], "workers": args.serve_workers},
+                       "eps": [0.1, 0.2], "workers": args.serve_workers, "walk_pool_attempts": pool_attempts,
+                       "walk_pool_build_s": pool_s,
+                       "walk_seed": "shared per graph" if pool_attempts else "per query"},
             "serial_solves_per_s": serial_rate, "served_vs_serial": best["solves_per_s"] / serial_rate,
-            "per_rate": per_rate, "identical_to_alone": bool(identical), "clocks": ck}
+            "per_rate": per_rate, "identical_to_alone": bool(identical),
+            "device_ms_by_phase_served": prof["phase_ms"], "clocks": ck}
     print(json.dumps(line), flush=True)
 
 
@@ -392,6 +413,7 @@ def main():
     ap.add_argument("--serve-rates", default="10,30,100,300")
     ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--serve-min-sources", type=int, default=16)
+    ap.add_argument("--serve-pool-attempts", type=float, default=0)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
