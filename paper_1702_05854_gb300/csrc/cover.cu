@@ -12,6 +12,8 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "solver.cuh"
@@ -78,6 +80,101 @@ __global__ void k_counts(const uint32_t* __restrict__ inv_off, uint32_t U, uint3
     cnt[r] = inv_off[r + 1] - inv_off[r];
 }
 
+// ------------------------------------------------------------------ dense strategy
+// Counts by atomics into a dense array over the element range [0, M), touched elements by
+// an exclusive scan of the nonzero flags (so uid stays increasing), the inverted index by
+// a counting fill (walks within one element's list in arrival order: the greedy treats a
+// list as a set, so results do not depend on that order).
+__global__ void k_dense_count(const int32_t* __restrict__ el, uint32_t E, uint32_t* __restrict__ dcnt) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < E; p += gridDim.x * blockDim.x)
+    atomicAdd(&dcnt[el[p]], 1u);
+}
+
+__global__ void k_dense_flags(const uint32_t* __restrict__ dcnt, int64_t M, uint32_t* __restrict__ didx) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < M; x += (int64_t)gridDim.x * blockDim.x)
+    didx[x] = dcnt[x] ? 1u : 0u;
+}
+
+// didx = exclusive scan of the flags: the unique index of each touched element
+__global__ void k_dense_unique(const uint32_t* __restrict__ dcnt, const uint32_t* __restrict__ didx, int64_t M,
+                               int32_t* __restrict__ uid, uint32_t* __restrict__ cnt) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < M; x += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = dcnt[x];
+    if (c) {
+      uid[didx[x]] = (int32_t)x;
+      cnt[didx[x]] = c;
+    }
+  }
+}
+
+// entry -> unique index, and the inverted index (cursor = dcnt, cleared beforehand)
+__global__ void k_dense_fill(const int32_t* __restrict__ el, uint32_t E, const uint32_t* __restrict__ wof,
+                             const uint32_t* __restrict__ didx, const uint32_t* __restrict__ inv_off,
+                             uint32_t* __restrict__ cursor, uint32_t* __restrict__ inv_walk,
+                             uint32_t* __restrict__ entry_uidx) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < E; p += gridDim.x * blockDim.x) {
+    const uint32_t r = didx[el[p]];
+    entry_uidx[p] = r;
+    inv_walk[inv_off[r] + atomicAdd(&cursor[r], 1u)] = wof[p];
+  }
+}
+
+static hsaw_status cover_build_dense(const int32_t* el, uint32_t E, int64_t M, int64_t count, Cover& cv,
+                                     cudaStream_t s) {
+  HSAW_TRY(cv.keys.ensure((size_t)M, s));   // dense counts, then the fill cursors
+  HSAW_TRY(cv.vals.ensure((size_t)M + 1, s));  // flags -> unique indices
+  HSAW_TRY(cv.keys2.ensure(E, s));          // walk of each entry
+  HSAW_TRY(cv.inv_walk.ensure(E, s));
+  HSAW_TRY(cv.entry_uidx.ensure(E, s));
+  uint32_t* dcnt = cv.keys.p;
+  uint32_t* didx = cv.vals.p;
+  uint32_t* wof = cv.keys2.p;
+  HSAW_CK(cudaMemsetAsync(dcnt, 0, (size_t)M * 4, s));
+  count_launch();
+  k_dense_count<<<grid_for(E, 256, 8192), 256, 0, s>>>(el, E, dcnt);
+  count_launch();
+  k_walk_of_entry<<<grid_for(count, 128, 8192), 128, 0, s>>>(cv.walk_eoff.p, (uint32_t)count, wof);
+  count_launch();
+  k_dense_flags<<<grid_for(M, 256, 8192), 256, 0, s>>>(dcnt, M, didx);
+  HSAW_CK(cudaGetLastError());
+  HSAW_TRY(exclusive_scan_u32(didx, (size_t)M, didx + M, s));
+  uint32_t U = 0;
+  HSAW_CK(cudaMemcpyAsync(&U, didx + M, 4, cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  cv.unique = U;
+  HSAW_TRY(cv.uid.ensure(U, s));
+  HSAW_TRY(cv.cnt.ensure(U, s));
+  HSAW_TRY(cv.inv_off.ensure((size_t)U + 1, s));
+  count_launch();
+  k_dense_unique<<<grid_for(M, 256, 8192), 256, 0, s>>>(dcnt, didx, M, cv.uid.p, cv.cnt.p);
+  HSAW_CK(cudaGetLastError());
+  HSAW_CK(cudaMemcpyAsync(cv.inv_off.p, cv.cnt.p, (size_t)U * 4, cudaMemcpyDeviceToDevice, s));
+  HSAW_TRY(exclusive_scan_u32(cv.inv_off.p, U, cv.inv_off.p + U, s));
+  HSAW_CK(cudaMemsetAsync(dcnt, 0, (size_t)U * 4, s));
+  count_launch();
+  k_dense_fill<<<grid_for(E, 256, 8192), 256, 0, s>>>(el, E, wof, didx, cv.inv_off.p, dcnt, cv.inv_walk.p,
+                                                      cv.entry_uidx.p);
+  HSAW_CK(cudaGetLastError());
+  return HSAW_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Strategy per (element range M, log2 of the entry count): the first call with both
+// strategies eligible times both (CUDA events) and keeps the faster for later calls.
+// HSAW_HIST=sort|dense in the environment forces one.
+enum HistStrategy { HIST_UNKNOWN = 0, HIST_SORT = 1, HIST_DENSE = 2 };
+static std::mutex g_tune_mu;
+static std::map<std::pair<int64_t, int>, int> g_tune;
+
+static int forced_strategy() {
+  const char* f = getenv("HSAW_HIST");
+  if (!f) return HIST_UNKNOWN;
+  return f[0] == 'd' ? HIST_DENSE : (f[0] == 's' ? HIST_SORT : HIST_UNKNOWN);
+}
+
+static hsaw_status cover_build_sort(const int32_t* el, uint32_t E, int64_t M, int64_t count, Cover& cv,
+                                    cudaStream_t s);
+
 hsaw_status cover_build(const Stream& st, hsaw_mode mode, int64_t first, int64_t count, Cover& cv, cudaStream_t s) {
   cv.walks = count;
   cv.entries = 0;
@@ -100,6 +197,46 @@ hsaw_status cover_build(const Stream& st, hsaw_mode mode, int64_t first, int64_t
   HSAW_CK(cudaGetLastError());
   if (E == 0) return HSAW_OK;
   const int32_t* el = em ? st.edges.p + (nb[0] - first) : st.nodes.p + nb[0];
+  const int64_t M = st.elem_range[em ? 1 : 0];
+  const bool dense_ok = M > 0 && M <= (1ll << 28) && M <= 64ll * (int64_t)E + (1 << 20);
+  int strat = forced_strategy();
+  if (strat == HIST_DENSE && !dense_ok) strat = HIST_SORT;
+  if (strat == HIST_UNKNOWN) {
+    if (!dense_ok) {
+      strat = HIST_SORT;
+    } else {
+      const std::pair<int64_t, int> key(M, bit_width(E));
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) strat = it->second;
+      }
+      if (strat == HIST_UNKNOWN) {  // time both once, keep the faster
+        cudaEvent_t ev[3];
+        for (auto& e : ev) HSAW_CK(cudaEventCreate(&e));
+        HSAW_CK(cudaEventRecord(ev[0], s));
+        hsaw_status a = cover_build_sort(el, E, M, count, cv, s);
+        HSAW_CK(cudaEventRecord(ev[1], s));
+        if (a == HSAW_OK) a = cover_build_dense(el, E, M, count, cv, s);
+        HSAW_CK(cudaEventRecord(ev[2], s));
+        HSAW_CK(cudaEventSynchronize(ev[2]));
+        float t_sort = 0.f, t_dense = 0.f;
+        cudaEventElapsedTime(&t_sort, ev[0], ev[1]);
+        cudaEventElapsedTime(&t_dense, ev[1], ev[2]);
+        for (auto& e : ev) cudaEventDestroy(e);
+        HSAW_TRY(a);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = t_dense < t_sort ? HIST_DENSE : HIST_SORT;
+        return HSAW_OK;
+      }
+    }
+  }
+  if (strat == HIST_DENSE) return cover_build_dense(el, E, M, count, cv, s);
+  return cover_build_sort(el, E, M, count, cv, s);
+}
+
+static hsaw_status cover_build_sort(const int32_t* el, uint32_t E, int64_t M, int64_t count, Cover& cv,
+                                    cudaStream_t s) {
   HSAW_TRY(cv.keys.ensure(E, s));
   HSAW_TRY(cv.vals.ensure(E, s));
   HSAW_TRY(cv.keys2.ensure(E, s));
@@ -112,7 +249,8 @@ hsaw_status cover_build(const Stream& st, hsaw_mode mode, int64_t first, int64_t
   HSAW_CK(cudaGetLastError());
   // the largest element id bounds the sort width
   bool alt = false;
-  HSAW_TRY(radix_sort_pairs(cv.keys.p, cv.vals.p, cv.keys2.p, cv.vals2.p, E, 31, s, &alt));
+  HSAW_TRY(radix_sort_pairs(cv.keys.p, cv.vals.p, cv.keys2.p, cv.vals2.p, E, M > 0 ? bit_width((uint64_t)(M - 1)) : 31,
+                            s, &alt));
   uint32_t* sk = alt ? cv.keys2.p : cv.keys.p;
   uint32_t* sv = alt ? cv.vals2.p : cv.vals.p;
   uint32_t* wof = alt ? cv.keys.p : cv.keys2.p;  // the free pair member

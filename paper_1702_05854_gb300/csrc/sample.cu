@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -351,6 +352,8 @@ static void launch_sample(const SampleParams& P, unsigned grid, cudaStream_t s) 
 
 hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_t want, cudaStream_t s) {
   SampleParams P = make_params(g, qd);
+  st.elem_range[0] = g.n;
+  st.elem_range[1] = g.m;
   const uint32_t CHUNK = 256;
   unsigned long long* d_steps = nullptr;
   HSAW_TRY(st.tmp64.ensure(1, s));
@@ -402,6 +405,8 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
         void* prof = profile_begin(s);
         launch_sample(P, grid, s);
         profile_end(prof, s, batch);
+        if (getenv("HSAW_LOG_LAUNCHES"))  // measurement aid: attempts of each sampler launch
+          fprintf(stderr, "hsaw: k_sample launch attempts=%llu\n", (unsigned long long)batch);
       }
       HSAW_CK(cudaGetLastError());
       count_launch();

@@ -38,6 +38,7 @@ struct Stream {
   DBuf<uint2> recs;
   DBuf<uint64_t> tmp64;
   double hit_rate = 0.0;  // running estimate for launch sizing
+  int64_t elem_range[2] = {0, 0};  // [node mode, edge mode]: element ids lie in [0, n) / [0, m)
   void release(cudaStream_t s);
 };
 

@@ -224,6 +224,21 @@ def test_greedy_grid_version_matches_oracle(c1_stream, monkeypatch):
         assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
 
 
+@pytest.mark.parametrize("strategy", ["sort", "dense"])
+def test_histogram_strategies_agree(c1_stream, monkeypatch, strategy):
+    """Sort-reduce and dense atomics give the same counts, and the same greedy."""
+    monkeypatch.setenv("HSAW_HIST", strategy)
+    d, g, og, w, st = c1_stream
+    for mode, M, k in ((hs.HSAW_EDGE, d["m"], 30), (hs.HSAW_NODE, d["n"], 30)):
+        uid, cnt = hs.hsaw_histogram(w, mode, 321, 15_000)
+        dense = st.histogram(mode, 321, 15_000, M)
+        nz = np.nonzero(dense)[0]
+        assert np.array_equal(uid, nz.astype(np.int32)) and np.array_equal(cnt, dense[nz])
+        ids, gains = hs.hsaw_greedy(w, g, mode, 321, 15_000, k)
+        oids, ogains = st.greedy(mode, 321, 15_000, M, k)
+        assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
+
+
 def test_greedy_zero_gain_fill():
     # every walk is covered after one pick; the rest are zero-gain smallest-id candidates
     n = 5
