@@ -135,7 +135,8 @@ typedef struct {
   int32_t rounds_t;      /* stopping-rule iterations (0 for FIXED_N) */
   uint64_t hits;         /* HSAWs used: |R| (FIXED_N) or |R_t| + |R'_t| */
   uint64_t attempts;     /* attempts up to and including the one that gave the last hit used */
-  uint64_t steps;        /* live-edge draws executed by the sampler (every launch) */
+  uint64_t steps;        /* live-edge draws the sampler executed (every launch; attempts served from a
+                            walk pool need none) - a throughput counter, not part of the result */
   uint64_t cov_R;        /* Cov_{R_t}(T) = sum of gains */
   uint64_t cov_Rprime;   /* Cov_{R'_t}(T) (0 for FIXED_N) */
   uint64_t hits_Rprime;  /* |R'_t| */

@@ -26,7 +26,6 @@ void Cover::release(cudaStream_t s) {
   keys.release(s); vals.release(s); keys2.release(s); vals2.release(s); run_flag.release(s);
   uid.release(s); cnt.release(s); inv_off.release(s); inv_walk.release(s); entry_uidx.release(s);
   walk_eoff.release(s); cnt_work.release(s); covered.release(s); dirty.release(s); partial.release(s);
-  misc.release(s);
 }
 
 // entry offsets of walks [first, first + count) relative to the first walk's first entry

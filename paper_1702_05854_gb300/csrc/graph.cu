@@ -212,7 +212,13 @@ static hsaw_status stage(const T* p, size_t count, bool on_device, cudaStream_t 
   }
   HSAW_TRY(dmalloc((void**)dev, count * sizeof(T), s));
   *owned = true;
-  HSAW_CK(cudaMemcpyAsync(*dev, p, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  const cudaError_t e = cudaMemcpyAsync(*dev, p, count * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    dfree(*dev, s);
+    *dev = nullptr;
+    *owned = false;
+    return cuda_fail(e, "cudaMemcpyAsync(graph input)", __FILE__, __LINE__);
+  }
   return HSAW_OK;
 }
 

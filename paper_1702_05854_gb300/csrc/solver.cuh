@@ -62,7 +62,6 @@ struct Cover {
   DBuf<uint32_t> cnt_work;                  // greedy's running counts
   DBuf<uint8_t> covered, dirty;  // greedy: walk covered flags, group dirty flags
   DBuf<unsigned long long> partial;
-  DBuf<uint32_t> misc;
   void release(cudaStream_t s);
 };
 
