@@ -296,6 +296,7 @@ def run_serve_mode(args, hs, torch):
     t_serial = time.perf_counter() - t0
     serial_rate = len(queries) / t_serial
     pool_s = 0.0
+    serial_pooled, serial_pooled_phase = None, None
     if pool_attempts:
         t0 = time.perf_counter()
         for g in graphs:
@@ -303,6 +304,14 @@ def run_serve_mode(args, hs, torch):
         torch.cuda.synchronize()
         pool_s = time.perf_counter() - t0
         hs.hsaw_solve(graphs[queries[0][0]], queries[0][1])
+        # serial again, now reading the pools: what reuse alone buys, and where time goes
+        hs.hsaw_profile_enable(True)
+        t0 = time.perf_counter()
+        for gi, q in queries:
+            hs.hsaw_solve(graphs[gi], q)
+        serial_pooled = len(queries) / (time.perf_counter() - t0)
+        serial_pooled_phase = hs.hsaw_profile_read()["phase_ms"]
+        hs.hsaw_profile_enable(False)
     rates = [float(x) for x in args.serve_rates.split(",")]
     per_rate = []
     identical = True
@@ -345,6 +354,7 @@ def run_serve_mode(args, hs, torch):
                        "walk_pool_build_s": pool_s,
                        "walk_seed": "shared per graph" if pool_attempts else "per query"},
             "serial_solves_per_s": serial_rate, "served_vs_serial": best["solves_per_s"] / serial_rate,
+            "serial_pooled_solves_per_s": serial_pooled, "serial_pooled_device_ms_by_phase": serial_pooled_phase,
             "per_rate": per_rate, "identical_to_alone": bool(identical),
             "device_ms_by_phase_served": prof["phase_ms"], "clocks": ck}
     print(json.dumps(line), flush=True)

@@ -57,30 +57,64 @@ __global__ void k_trace(const uint4* __restrict__ node, const uint2* __restrict_
 }
 
 // First real source on each trace of attempts [a0, a0 + n_attempts) (launch offsets).
+// One warp per 32 consecutive attempts: their traces are contiguous in the pool, so the
+// lanes stride over the concatenated nodes with coalesced loads; a source at position q
+// belongs to the trace whose offset range holds q (binary search over the trace starts,
+// one per lane), and the first such position of each trace is kept in shared memory.
 template <bool HAS_P>
-__global__ void k_pool_scan(const uint64_t* __restrict__ off, const int32_t* __restrict__ nodes,
-                            const uint32_t* __restrict__ s_bits, const uint32_t* __restrict__ p32, uint32_t k0,
-                            uint32_t k1, uint64_t a0, uint32_t n_attempts, uint32_t chunk, uint32_t cap,
-                            uint32_t* __restrict__ chunk_hits, uint2* __restrict__ recs, uint32_t* __restrict__ status) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_attempts; i += gridDim.x * blockDim.x) {
-    const uint64_t a = a0 + i;
-    const uint64_t b = off[a], e = off[a + 1];
-    uint32_t hit_len = 0;
-    for (uint64_t q = b; q < e; ++q) {
-      const uint32_t u = (uint32_t)__ldg(&nodes[q]);
-      if ((__ldg(&s_bits[u >> 5]) >> (u & 31)) & 1u) {
-        if (!HAS_P || source_coin(node_draw(a, u, k0, k1).y, __ldg(&p32[u]))) {
-          hit_len = (uint32_t)(q - b + 1);
-          break;
+__global__ void __launch_bounds__(256) k_pool_scan(const uint64_t* __restrict__ off, const int32_t* __restrict__ nodes,
+                                                   const uint32_t* __restrict__ s_bits,
+                                                   const uint32_t* __restrict__ p32, uint32_t k0, uint32_t k1,
+                                                   uint64_t a0, uint32_t n_attempts, uint32_t chunk, uint32_t cap,
+                                                   uint32_t* __restrict__ chunk_hits, uint2* __restrict__ recs,
+                                                   uint32_t* __restrict__ status) {
+  __shared__ uint32_t first_hit[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t groups = (n_attempts + 31) / 32;
+  for (uint32_t gi = blockIdx.x * 8 + w; gi < groups; gi += gridDim.x * 8) {
+    const uint32_t i0 = gi * 32;
+    const uint32_t cnt = min(32u, n_attempts - i0);
+    const uint64_t my_off = off[a0 + i0 + min((uint32_t)lane, cnt)];  // lane t holds the start of trace t
+    const uint64_t b = __shfl_sync(0xffffffffu, my_off, 0);
+    const uint64_t e = off[a0 + i0 + cnt];  // end of the group's last trace (the 33rd offset)
+    first_hit[w][lane] = 0xFFFFFFFFu;
+    __syncwarp();
+    for (uint64_t q0 = b; q0 < e; q0 += 32) {
+      const uint64_t q = q0 + lane;
+      bool src = false;
+      uint32_t u = 0;
+      if (q < e) {
+        u = (uint32_t)__ldg(&nodes[q]);
+        src = (__ldg(&s_bits[u >> 5]) >> (u & 31)) & 1u;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, src);
+      if (!m) continue;
+      // trace of position q: largest t with off[t] <= q (search over the lanes' offsets)
+      uint32_t lo = 0, hi = cnt - 1;
+      for (int it = 0; it < 6; ++it) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        const uint64_t om = __shfl_sync(0xffffffffu, my_off, mid);
+        if (lo < hi) {
+          if (om <= q) lo = mid; else hi = mid - 1;
         }
       }
+      const uint64_t trace_start = __shfl_sync(0xffffffffu, my_off, lo);  // every lane takes part
+      if (src) {
+        const uint32_t t = lo;
+        bool real = true;
+        if (HAS_P) real = source_coin(node_draw(a0 + i0 + t, u, k0, k1).y, __ldg(&p32[u]));
+        if (real) atomicMin(&first_hit[w][t], (uint32_t)(q - trace_start));
+      }
     }
-    if (hit_len) {
+    __syncwarp();
+    if ((uint32_t)lane < cnt && first_hit[w][lane] != 0xFFFFFFFFu) {
+      const uint32_t i = i0 + lane;
       const uint32_t ck = i / chunk;
       const uint32_t slot = atomicAdd(&chunk_hits[ck], 1u);
-      if (slot < cap) recs[(size_t)ck * cap + slot] = make_uint2(i, hit_len);
+      if (slot < cap) recs[(size_t)ck * cap + slot] = make_uint2(i, first_hit[w][lane] + 1);
       else atomicOr(status, 1u);
     }
+    __syncwarp();
   }
 }
 
@@ -169,7 +203,7 @@ hsaw_status pool_build(Graph& g, uint64_t seed, uint64_t attempts, cudaStream_t 
 void pool_scan_launch(const Graph& g, const QueryDev& qd, uint64_t a0, uint32_t n_attempts, uint32_t chunk,
                       uint32_t cap, uint32_t* chunk_hits, uint2* recs, uint32_t* status, cudaStream_t s) {
   const uint32_t k0 = (uint32_t)qd.seed, k1 = (uint32_t)(qd.seed >> 32);
-  const unsigned grid = grid_for(n_attempts, 256, (unsigned)sm_count() * 8);
+  const unsigned grid = grid_for((n_attempts + 31) / 32, 8, (unsigned)sm_count() * 8);
   count_launch();
   if (qd.p32)
     k_pool_scan<true><<<grid, 256, 0, s>>>(g.pool.off, g.pool.nodes, qd.s_bits, qd.p32, k0, k1, a0, n_attempts, chunk,
