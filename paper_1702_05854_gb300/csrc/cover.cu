@@ -729,11 +729,27 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  const bool log = getenv("HSAW_LOG_LAUNCHES") != nullptr;  // measurement aid
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (log) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, s);
+  }
   count_launch();
   HSAW_CK(cudaLaunchKernelEx(&cfg, k_greedy_cluster, P));
   uint32_t h[4];
   HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
+  if (log) cudaEventRecord(ev1, s);
   HSAW_CK(cudaStreamSynchronize(s));
+  if (log) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    fprintf(stderr, "hsaw: k_greedy_cluster walks=%lld entries=%lld unique=%u cluster=%u gshift=%u k=%d ms=%.3f\n",
+            (long long)cv.walks, (long long)cv.entries, U, csize, gshift, k, ms);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
   *rounds = (int32_t)h[3];
   *done = true;
   return HSAW_OK;
