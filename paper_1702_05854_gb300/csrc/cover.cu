@@ -442,6 +442,8 @@ __global__ void __launch_bounds__(512) k_greedy(GreedyParams P) {
 // on global memory.  Group g covers elements [g << gshift, (g + 1) << gshift).
 namespace cg = cooperative_groups;
 
+constexpr unsigned long long KEY_UNKNOWN = ~0ull;  // above every element key (counts < 2^31)
+
 struct ClusterGreedyParams {
   uint32_t U, NG, per_cta, gshift;
   uint32_t short_walks;  // 1: walks average few elements, cover one walk per thread
@@ -459,8 +461,8 @@ struct ClusterGreedyParams {
 
 __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams P) {
   extern __shared__ unsigned long long gkey[];  // per: largest key of each owned group
-  __shared__ unsigned long long red[33];
-  __shared__ unsigned long long cta_best;
+  __shared__ unsigned long long red[32];
+  __shared__ unsigned long long slot[16];  // largest key of each CTA of the cluster
   cg::cluster_group cluster = cg::this_cluster();
   const uint32_t rank = cluster.block_rank();
   const uint32_t C = cluster.num_blocks();
@@ -472,22 +474,34 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
   const uint32_t gend = min(P.NG, gbase + per);
   const uint32_t nown = gend > gbase ? gend - gbase : 0;
   for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dbits[i] = 0xFFFFFFFFu;
-  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) gkey[i] = 0;
+  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) gkey[i] = KEY_UNKNOWN;
   cluster.sync();
   const uint32_t gsz = 1u << P.gshift;
   int32_t r = 0;
   for (; r < P.k; ++r) {
-    // 1. refresh the owned groups whose counts changed (one warp per word of dirty bits)
+    // 1. refresh the owned groups whose counts changed.  Counts only go down, so a group
+    //    keeps its largest key unless the count of that key's own element changed: one lane
+    //    per dirty group re-reads that one count, and only the groups whose largest element
+    //    changed are rescanned, one warp per group.
     for (uint32_t wi = w; wi < words; wi += nw) {
-      uint32_t bits = dbits[wi];
+      const uint32_t bits = dbits[wi];
       __syncwarp();
       if (!bits) continue;
       if (lane == 0) dbits[wi] = 0;
-      while (bits) {
-        const uint32_t b = __ffs(bits) - 1;
-        bits &= bits - 1;
+      const uint32_t gl0 = wi * 32 + lane;
+      bool stale = false;
+      if (((bits >> lane) & 1u) && gl0 < nown) {
+        const unsigned long long k0 = gkey[gl0];
+        if (k0 == KEY_UNKNOWN)
+          stale = true;
+        else if (k0 != 0)  // a group whose keys are all zero stays so
+          stale = __ldcg(&P.cnt[0xFFFFFFFFu - (uint32_t)k0]) != (uint32_t)(k0 >> 32);
+      }
+      uint32_t todo = __ballot_sync(0xffffffffu, stale);
+      while (todo) {
+        const uint32_t b = __ffs(todo) - 1;
+        todo &= todo - 1;
         const uint32_t gl = wi * 32 + b;
-        if (gl >= nown) continue;
         const uint32_t e0 = (gbase + gl) << P.gshift;
         const uint32_t e1 = min(P.U, e0 + gsz);
         unsigned long long best = 0;
@@ -500,15 +514,21 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
       }
     }
     __syncthreads();
-    // 2. cluster-wide argmax of (count, smallest id)
+    // 2. cluster-wide argmax of (count, smallest id): each CTA pushes its largest key into
+    //    slot[rank] of every CTA, then every warp reduces the slots it holds
     unsigned long long key = 0;
     for (uint32_t gl = threadIdx.x; gl < nown; gl += blockDim.x) key = gkey[gl] > key ? gkey[gl] : key;
-    key = block_max_u64(key, red);
-    if (threadIdx.x == 0) cta_best = key;
+    key = warp_max_u64(key);
+    if (lane == 0) red[w] = key;
+    __syncthreads();
+    if (w == 0) {
+      key = lane < nw ? red[lane] : 0ull;
+      key = warp_max_u64(key);
+      if (lane < (int)C) *cluster.map_shared_rank(&slot[rank], lane) = key;
+    }
     cluster.sync();
-    key = 0;
-    if (threadIdx.x < C) key = *cluster.map_shared_rank(&cta_best, threadIdx.x);
-    key = block_max_u64(key, red);
+    key = lane < (int)C ? slot[lane] : 0ull;
+    key = warp_max_u64(key);
     const uint32_t gain = (uint32_t)(key >> 32);
     if (gain == 0) break;  // every remaining gain is zero: the same decision in every CTA
     const uint32_t u = 0xFFFFFFFFu - (uint32_t)key;
@@ -674,8 +694,8 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   const size_t smem_cap = cfg0.smem_cap;
   if (!cluster_size) return HSAW_OK;
   const uint32_t U = (uint32_t)cv.unique;
-  // the smallest cluster (fewest SMs, cheapest barrier) whose shared memory holds the keys
-  // of 256-element groups; beyond the largest cluster, larger groups
+  // a cluster whose shared memory holds the keys of 256-element groups; beyond the largest
+  // cluster, larger groups
   auto need = [](uint32_t per) { return (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64; };
   uint32_t gshift = 8, csize = 1;
   uint32_t NG = (uint32_t)(((uint64_t)U + 255) >> 8), per = NG;
