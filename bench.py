@@ -285,6 +285,11 @@ def run_serve_mode(args, hs, torch):
         gm.append((n, int(src.shape[0])))
     qs = serve_queries(args.serve_queries, gm, args.serve_min_sources)
     pool_attempts = int(args.serve_pool_attempts)
+    # pool sizes in proportion to the graph's nodes (hit rates fall as 1/n for the same
+    # source-set sizes), whole index blocks of 2^22 attempts, the largest graph getting
+    # --serve-pool-attempts
+    n_max = max(n for n, _ in gm)
+    pool_sizes = [max(1 << 22, (pool_attempts * n // n_max) >> 22 << 22) if pool_attempts else 0 for n, _ in gm]
     if pool_attempts:  # every query on a graph shares its walk seed, so traces can be reused
         for _, kw in qs:
             kw["seed"] = synth.SEED_WALKS
@@ -295,14 +300,16 @@ def run_serve_mode(args, hs, torch):
     alone = [hs.hsaw_solve(graphs[gi], q) for gi, q in queries]
     t_serial = time.perf_counter() - t0
     serial_rate = len(queries) / t_serial
-    pool_s = 0.0
+    pool_s, pool_gb = 0.0, 0.0
     serial_pooled, serial_pooled_phase = None, None
     if pool_attempts:
+        free0 = torch.cuda.mem_get_info()[0]
         t0 = time.perf_counter()
-        for g in graphs:
-            g.build_walk_pool(synth.SEED_WALKS, pool_attempts)
+        for g, pa in zip(graphs, pool_sizes):
+            g.build_walk_pool(synth.SEED_WALKS, pa)
         torch.cuda.synchronize()
         pool_s = time.perf_counter() - t0
+        pool_gb = (free0 - torch.cuda.mem_get_info()[0]) / 1e9
         hs.hsaw_solve(graphs[queries[0][0]], queries[0][1])
         # serial again, now reading the pools: what reuse alone buys, and where time goes
         hs.hsaw_profile_enable(True)
@@ -350,8 +357,8 @@ def run_serve_mode(args, hs, torch):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "serving", "graphs": [f"rmat{sc}-wc" for sc in scales],
                        "queries_per_rate": len(queries), "sources": [args.serve_min_sources, 1000], "k": [10, 1000],
-                       "eps": [0.1, 0.2], "workers": args.serve_workers, "walk_pool_attempts": pool_attempts,
-                       "walk_pool_build_s": pool_s,
+                       "eps": [0.1, 0.2], "workers": args.serve_workers, "walk_pool_attempts": pool_sizes,
+                       "walk_pool_build_s": pool_s, "walk_pool_gb": round(pool_gb, 2),
                        "walk_seed": "shared per graph" if pool_attempts else "per query"},
             "serial_solves_per_s": serial_rate, "served_vs_serial": best["solves_per_s"] / serial_rate,
             "serial_pooled_solves_per_s": serial_pooled, "serial_pooled_device_ms_by_phase": serial_pooled_phase,

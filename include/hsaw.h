@@ -100,13 +100,17 @@ HSAW_API hsaw_status hsaw_graph_edge(hsaw_graph g, int64_t edge_id, int32_t* src
 /* Walk pool (not in the paper; serving many queries on one graph).  Attempt a's walk
  * ignoring sources - its nodes until no live in-edge or a cycle - does not depend on the
  * query: a query's HSAW of attempt a is that trace's prefix up to its first real source
- * (same node-keyed draws and coins).  hsaw_graph_build_walk_pool stores the traces of
- * attempts [0, attempts) for walk seed `seed` on the device (about 8 B per trace node);
- * afterwards every solve, sample or served query on g with q->seed == seed and no removed
- * elements scans these traces for its attempts below `attempts` instead of walking them,
- * and samples the rest as usual, with bit-identical results.  Building replaces any
- * previous pool; do not build or drop while other calls use g.  HSAW_E_NOMEM if the
- * traces do not fit.  hsaw_graph_drop_walk_pool frees it. */
+ * (same node-keyed draws and coins), so attempt a hits exactly when its trace holds a real
+ * source.  hsaw_graph_build_walk_pool walks attempts [0, attempts) for walk seed `seed`
+ * and keeps, per block of 2^22 attempts, each node's list of the attempts whose trace
+ * passes through it (about 4 B per trace node, plus 4 (n + 1) B per block).  Afterwards
+ * every solve, sample or served query on g with q->seed == seed and no removed elements
+ * takes its hits among attempts below `attempts` from its sources' lists (re-walking only
+ * the hits), and samples the rest as usual, with bit-identical results.  Building
+ * replaces any previous pool; do not build or drop while other calls use g.  Errors:
+ * HSAW_E_NOMEM if the index does not fit, HSAW_E_INVALID for more than 2^32 attempts or a
+ * block whose traces exceed 2^32 nodes, HSAW_E_STEP_CAP.  hsaw_graph_drop_walk_pool frees
+ * it. */
 HSAW_API hsaw_status hsaw_graph_build_walk_pool(hsaw_graph g, uint64_t seed, uint64_t attempts, void* stream);
 HSAW_API hsaw_status hsaw_graph_drop_walk_pool(hsaw_graph g);
 

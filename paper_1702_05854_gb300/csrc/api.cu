@@ -141,6 +141,10 @@ static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cu
       if (cancel_requested()) return fail(HSAW_E_CANCELLED, "solve: query cancelled");
       if (t > 40 || (L << (t - 1)) > (int64_t)1 << 30) return fail(HSAW_E_NOMEM, "stop rule: sample budget beyond device limits");
       const int64_t half = L << (t - 1);
+      // Check stops the rule only when Cov_{R'_t}(T) >= Lambda1, and Cov_{R'_t}(T) <= |R'_t|:
+      // a round with |R'_t| < Lambda1 (always t = 1, as L < Lambda1) that is not the last one
+      // cannot end the loop, and every result field is rewritten by a later round
+      if ((double)half < lam1 && !((double)half >= n_max || (double)t >= t_max)) continue;
       void* ph = phase_begin(s);
       HSAW_TRY(stream_extend(g, W.qd, W.st, 2 * half, s));
       phase_end(ph, s, PH_SAMPLE);

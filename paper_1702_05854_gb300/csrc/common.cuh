@@ -71,17 +71,23 @@ struct DBuf {  // grow-only device buffer
 // b = floor(r * deg / in-sum) in [0, deg), guide[first(v) + b] = the live in-edge index of
 // the smallest draw of the bucket, ceil(b * in-sum / deg); the answer for any r of the
 // bucket is at or after it (Chen & Asau's guide table), usually within a step or two.
-// Walk pool (query-independent traces): for walk seed `seed`, trace a (a < attempts) is
-// attempt a's walk ignoring sources - its nodes until no live in-edge or a detected cycle
-// (nodes[off[a] .. off[a+1]), edges from off[a] - a).  A query's HSAW of attempt a is the
-// trace's prefix up to its first real source (the source test is per node, with the same
-// node-keyed coin), so queries with this seed scan traces instead of re-walking.
+// Walk pool (query-independent traces, kept as an inverted index): for walk seed `seed`,
+// trace a (a < attempts) is attempt a's walk ignoring sources - its nodes until no live
+// in-edge or a detected cycle.  A query's HSAW of attempt a is the trace's prefix up to its
+// first real source (the source test is per node, with the same node-keyed coin), so
+// attempt a hits exactly when its trace holds a real source.  Attempts are grouped in
+// blocks of 2^shift; for block b and node v, ent[boff[b] + noff[b (n + 1) + v] ..
+// boff[b] + noff[b (n + 1) + v + 1]) lists (in no particular order, possibly twice) the
+// attempts a - (b << shift) of the block whose trace passes through v.
 struct WalkPool {
   uint64_t seed = 0;
   uint64_t attempts = 0;
-  uint64_t* off = nullptr;
-  int32_t* nodes = nullptr;
-  int32_t* edges = nullptr;
+  uint32_t shift = 0;
+  uint32_t blocks = 0;
+  uint64_t entries = 0;
+  uint64_t* boff = nullptr;  // blocks + 1
+  uint32_t* noff = nullptr;  // blocks * (n + 1)
+  uint32_t* ent = nullptr;   // entries
 };
 
 struct Graph {

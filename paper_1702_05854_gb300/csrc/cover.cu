@@ -548,10 +548,11 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
     if (P.short_walks) {
       for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
         const uint32_t j = P.inv_walk[q];
-        if (__ldcg(&P.covered[j])) continue;
+        const uint8_t was = __ldcg(&P.covered[j]);
+        const uint32_t p0 = P.walk_eoff[j], p1 = P.walk_eoff[j + 1];  // in flight with the flag
+        if (was) continue;
         P.covered[j] = 1;
-        const uint32_t p1 = P.walk_eoff[j + 1];
-        for (uint32_t p = P.walk_eoff[j]; p < p1; ++p) {
+        for (uint32_t p = p0; p < p1; ++p) {
           const uint32_t x = P.entry_uidx[p];
           atomicSub(&P.cnt[x], 1u);
           const uint32_t gg = x >> P.gshift, gl = gg % per;
@@ -563,14 +564,12 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
     for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
       const uint32_t j = P.inv_walk[q];
       uint32_t fresh = 0;
-      if (lane == 0) {
-        fresh = __ldcg(&P.covered[j]) ? 0u : 1u;
-        if (fresh) P.covered[j] = 1;
-      }
+      if (lane == 0) fresh = __ldcg(&P.covered[j]) ? 0u : 1u;
+      const uint32_t p0 = P.walk_eoff[j], p1 = P.walk_eoff[j + 1];  // in flight with the flag
       fresh = __shfl_sync(0xffffffffu, fresh, 0);
       if (!fresh) continue;
-      const uint32_t p1 = P.walk_eoff[j + 1];
-      for (uint32_t p = P.walk_eoff[j] + lane; p < p1; p += 32) {
+      if (lane == 0) P.covered[j] = 1;
+      for (uint32_t p = p0 + lane; p < p1; p += 32) {
         const uint32_t x = P.entry_uidx[p];
         atomicSub(&P.cnt[x], 1u);
         const uint32_t gg = x >> P.gshift, gl = gg % per;

@@ -271,25 +271,31 @@ hsaw_status query_upload(const Graph& g, const hsaw_query* q, QueryDev& qd, cuda
     HSAW_TRY(dmalloc((void**)&qd.p32, (size_t)g.n * 4, s));
     HSAW_CK(cudaMemsetAsync(qd.p32, 0, (size_t)g.n * 4, s));
   }
-  int32_t* d_src = nullptr;
+  // the source list stays with the query (walk-pool queries read their sources' lists);
+  // on failure the caller's query_release frees what was allocated
+  HSAW_TRY(dmalloc((void**)&qd.s_list, (size_t)q->n_sources * 4, s));
+  qd.n_src = q->n_sources;
+  HSAW_CK(cudaMemcpyAsync(qd.s_list, q->sources, (size_t)q->n_sources * 4, cudaMemcpyHostToDevice, s));
   uint32_t* d_p = nullptr;
-  HSAW_TRY(dmalloc((void**)&d_src, (size_t)q->n_sources * 4, s));
-  HSAW_CK(cudaMemcpyAsync(d_src, q->sources, (size_t)q->n_sources * 4, cudaMemcpyHostToDevice, s));
   if (q->p_fixed) {
     HSAW_TRY(dmalloc((void**)&d_p, (size_t)q->n_sources * 4, s));
-    HSAW_CK(cudaMemcpyAsync(d_p, q->p_fixed, (size_t)q->n_sources * 4, cudaMemcpyHostToDevice, s));
+    if (cudaMemcpyAsync(d_p, q->p_fixed, (size_t)q->n_sources * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      dfree(d_p, s);
+      return fail(HSAW_E_DEVICE, "query: probability upload failed");
+    }
   }
   count_launch();
-  k_set_bits<<<grid_for(q->n_sources, 256, 1024), 256, 0, s>>>(d_src, d_p, q->n_sources, qd.s_bits, qd.p32);
-  HSAW_CK(cudaGetLastError());
-  dfree(d_src, s);
+  k_set_bits<<<grid_for(q->n_sources, 256, 1024), 256, 0, s>>>(qd.s_list, d_p, q->n_sources, qd.s_bits, qd.p32);
+  const cudaError_t le = cudaGetLastError();
   dfree(d_p, s);
+  if (le != cudaSuccess) return fail(HSAW_E_DEVICE, "query: suspect bits launch failed");
   qd.seed = q->seed;
   return HSAW_OK;
 }
 
 void query_release(QueryDev& qd, cudaStream_t s) {
   dfree(qd.s_bits, s);
+  dfree(qd.s_list, s);
   dfree(qd.p32, s);
   if (qd.owns_removed) {
     dfree(qd.edge_removed, s);
@@ -301,6 +307,7 @@ void query_release(QueryDev& qd, cudaStream_t s) {
 void Stream::release(cudaStream_t s) {
   aid.release(s); len.release(s); node_off.release(s); nodes.release(s); edges.release(s);
   chunk_hits.release(s); chunk_off.release(s); ctrs.release(s); recs.release(s); tmp64.release(s);
+  pbits.release(s); pcnt.release(s);
 }
 
 hsaw_status stream_init(Stream& st, uint64_t first_attempt, uint64_t max_attempts, cudaStream_t s) {
@@ -350,21 +357,86 @@ static void launch_sample(const SampleParams& P, unsigned grid, cudaStream_t s) 
   else { count_launch(); k_sample<false, false><<<grid, 256, 0, s>>>(P); }
 }
 
-hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_t want, cudaStream_t s) {
+// One sampler launch over attempts [st.next_attempt, + batch): hits are recorded per chunk
+// and compacted in attempt order into aid/len at st.count; *new_hits receives their number.
+static hsaw_status sample_window(const Graph& g, const QueryDev& qd, Stream& st, uint64_t batch, uint32_t* new_hits,
+                                 cudaStream_t s) {
   SampleParams P = make_params(g, qd);
+  const uint32_t CHUNK = 256;
+  const uint32_t n_chunks = (uint32_t)((batch + CHUNK - 1) / CHUNK);
+  // records per chunk: a few standard deviations above the expected hits, else all
+  double exp_hits = std::max(st.hit_rate, 0.0) * CHUNK;
+  uint32_t cap = (uint32_t)std::min<double>(CHUNK, std::ceil(exp_hits + 6.0 * std::sqrt(exp_hits + 1.0) + 8.0));
+  if (st.hit_rate == 0.0) cap = CHUNK;
+  for (;;) {
+    HSAW_TRY(st.tmp64.ensure(1, s));
+    HSAW_TRY(st.chunk_hits.ensure(n_chunks, s));
+    HSAW_TRY(st.chunk_off.ensure(n_chunks, s));
+    HSAW_TRY(st.recs.ensure((size_t)n_chunks * cap, s));
+    HSAW_CK(cudaMemsetAsync(st.chunk_hits.p, 0, (size_t)n_chunks * 4, s));
+    HSAW_CK(cudaMemsetAsync(st.ctrs.p, 0, 8 * 4, s));
+    unsigned long long* d_steps = reinterpret_cast<unsigned long long*>(st.tmp64.p);
+    HSAW_CK(cudaMemsetAsync(d_steps, 0, 8, s));
+    P.a0 = st.next_attempt;
+    P.n_attempts = (uint32_t)batch;
+    P.chunk = CHUNK;
+    P.n_chunks = n_chunks;
+    P.cap = cap;
+    P.chunk_ctr = st.ctrs.p;
+    P.chunk_hits = st.chunk_hits.p;
+    P.recs = st.recs.p;
+    P.steps = d_steps;
+    const unsigned grid = (unsigned)std::max(1, std::min<int>(sm_count() * sample_blocks_per_sm(),
+                                                               (int)((n_chunks + 7) / 8)));
+    void* prof = profile_begin(s);
+    launch_sample(P, grid, s);
+    profile_end(prof, s, batch);
+    if (getenv("HSAW_LOG_LAUNCHES"))  // measurement aid: attempts of each sampler launch
+      fprintf(stderr, "hsaw: k_sample launch attempts=%llu\n", (unsigned long long)batch);
+    HSAW_CK(cudaGetLastError());
+    count_launch();
+    k_clamp<<<grid_for(n_chunks, 256, 4096), 256, 0, s>>>(st.chunk_hits.p, st.chunk_off.p, n_chunks, cap);
+    HSAW_CK(cudaGetLastError());
+    HSAW_TRY(exclusive_scan_u32(st.chunk_off.p, n_chunks, st.ctrs.p + 2, s));
+    uint32_t h[4];
+    unsigned long long hs = 0;
+    HSAW_CK(cudaMemcpyAsync(h, st.ctrs.p, 16, cudaMemcpyDeviceToHost, s));
+    HSAW_CK(cudaMemcpyAsync(&hs, d_steps, 8, cudaMemcpyDeviceToHost, s));
+    HSAW_CK(cudaStreamSynchronize(s));
+    if (h[1] & ST_STEP_CAP) return fail(HSAW_E_STEP_CAP, "sampling: a walk exceeded its step guard");
+    if ((h[1] & ST_OVERFLOW) && cap < CHUNK) {
+      cap = CHUNK;  // rare: rerun this launch with room for every attempt to hit
+      continue;
+    }
+    st.steps += hs;
+    profile_add_steps(hs);
+    *new_hits = h[2];
+    if (h[2]) {
+      HSAW_TRY(st.aid.ensure((size_t)st.count + h[2], s, true));
+      HSAW_TRY(st.len.ensure((size_t)st.count + h[2], s, true));
+      count_launch();
+      k_compact<<<grid_for((size_t)n_chunks * 32, 256, 8192), 256, 0, s>>>(
+          st.chunk_hits.p, st.chunk_off.p, st.recs.p, cap, n_chunks, st.next_attempt, st.aid.p + st.count,
+          st.len.p + st.count);
+      HSAW_CK(cudaGetLastError());
+    }
+    return HSAW_OK;
+  }
+}
+
+hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_t want, cudaStream_t s) {
   st.elem_range[0] = g.n;
   st.elem_range[1] = g.m;
   const uint32_t CHUNK = 256;
-  unsigned long long* d_steps = nullptr;
-  HSAW_TRY(st.tmp64.ensure(1, s));
-  // traces of the walk pool serve this query's attempts below pool.attempts when the walk
-  // seed matches and the graph is not a residual one
-  const bool pool_ok = g.pool.nodes && g.pool.seed == qd.seed && !qd.edge_removed && !qd.node_removed;
+  const uint32_t k0 = (uint32_t)qd.seed, k1 = (uint32_t)(qd.seed >> 32);
+  // the walk pool serves this query's attempts below pool.attempts when the walk seed
+  // matches and the graph is not a residual one
+  const bool pool_ok = g.pool.ent && g.pool.seed == qd.seed && qd.s_list && !qd.edge_removed && !qd.node_removed;
   while (st.count < want) {
     if (cancel_requested()) return fail(HSAW_E_CANCELLED, "sampling: query cancelled");
     const uint64_t used = st.next_attempt - st.first_attempt;
     if (used >= st.max_attempts) return fail(HSAW_E_TIMEOUT, "sampling: attempt budget exhausted before enough hits");
-    // launch size from the hit rate so far (2^20 .. 2^28 attempts; doubling while no hit)
+    // window size from the hit rate so far (2^20 .. 2^28 attempts; doubling while no hit)
     const double need = (double)(want - st.count);
     st.hit_rate = used ? (double)st.count / (double)used : 0.0;
     double target = st.hit_rate > 0 ? need / st.hit_rate * 1.05 + 4096.0 : std::max(1048576.0, 2.0 * (double)used);
@@ -372,100 +444,45 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
     target = std::min(target, 268435456.0);
     uint64_t batch = (uint64_t)target;
     batch = std::min<uint64_t>(batch, st.max_attempts - used);
-    batch = (batch + CHUNK - 1) / CHUNK * CHUNK;
-    const bool pooled = pool_ok && st.next_attempt < g.pool.attempts;
-    if (pooled) batch = std::min<uint64_t>(batch, g.pool.attempts - st.next_attempt);  // scans stop at the pool's end
-    const uint32_t n_chunks = (uint32_t)((batch + CHUNK - 1) / CHUNK);
-    // records per chunk: a few standard deviations above the expected hits, else all
-    double exp_hits = std::max(st.hit_rate, 0.0) * CHUNK;
-    uint32_t cap = (uint32_t)std::min<double>(CHUNK, std::ceil(exp_hits + 6.0 * std::sqrt(exp_hits + 1.0) + 8.0));
-    if (st.hit_rate == 0.0) cap = CHUNK;
-    for (int attempt_cap = 0; attempt_cap < 2; ++attempt_cap) {
-      HSAW_TRY(st.chunk_hits.ensure(n_chunks, s));
-      HSAW_TRY(st.chunk_off.ensure(n_chunks, s));
-      HSAW_TRY(st.recs.ensure((size_t)n_chunks * cap, s));
-      HSAW_CK(cudaMemsetAsync(st.chunk_hits.p, 0, (size_t)n_chunks * 4, s));
-      HSAW_CK(cudaMemsetAsync(st.ctrs.p, 0, 8 * 4, s));
-      d_steps = reinterpret_cast<unsigned long long*>(st.tmp64.p);
-      HSAW_CK(cudaMemsetAsync(d_steps, 0, 8, s));
-      P.a0 = st.next_attempt;
-      P.n_attempts = (uint32_t)batch;
-      P.chunk = CHUNK;
-      P.n_chunks = n_chunks;
-      P.cap = cap;
-      P.chunk_ctr = st.ctrs.p;
-      P.chunk_hits = st.chunk_hits.p;
-      P.recs = st.recs.p;
-      P.steps = d_steps;
-      const unsigned grid = (unsigned)std::max(1, std::min<int>(sm_count() * sample_blocks_per_sm(),
-                                                                 (int)((n_chunks + 7) / 8)));
-      if (pooled) {
-        pool_scan_launch(g, qd, P.a0, P.n_attempts, CHUNK, cap, st.chunk_hits.p, st.recs.p, st.ctrs.p + 3, s);
-      } else {
-        void* prof = profile_begin(s);
-        launch_sample(P, grid, s);
-        profile_end(prof, s, batch);
-        if (getenv("HSAW_LOG_LAUNCHES"))  // measurement aid: attempts of each sampler launch
-          fprintf(stderr, "hsaw: k_sample launch attempts=%llu\n", (unsigned long long)batch);
-      }
-      HSAW_CK(cudaGetLastError());
-      count_launch();
-      k_clamp<<<grid_for(n_chunks, 256, 4096), 256, 0, s>>>(st.chunk_hits.p, st.chunk_off.p, n_chunks, cap);
-      HSAW_CK(cudaGetLastError());
-      HSAW_TRY(exclusive_scan_u32(st.chunk_off.p, n_chunks, st.ctrs.p + 2, s));
-      uint32_t h[4];
-      unsigned long long hs = 0;
-      HSAW_CK(cudaMemcpyAsync(h, st.ctrs.p, 16, cudaMemcpyDeviceToHost, s));
-      HSAW_CK(cudaMemcpyAsync(&hs, d_steps, 8, cudaMemcpyDeviceToHost, s));
-      HSAW_CK(cudaStreamSynchronize(s));
-      if (h[1] & ST_STEP_CAP) return fail(HSAW_E_STEP_CAP, "sampling: a walk exceeded its step guard");
-      if (((h[1] & ST_OVERFLOW) || h[3]) && cap < CHUNK) {
-        cap = CHUNK;  // rare: rerun this launch with room for every attempt to hit
-        continue;
-      }
-      const uint32_t new_hits = h[2];
-      st.steps += hs;
-      profile_add_steps(hs);
-      // append the ordered hits
-      HSAW_TRY(st.aid.ensure((size_t)st.count + new_hits, s, true));
-      HSAW_TRY(st.len.ensure((size_t)st.count + new_hits, s, true));
-      HSAW_TRY(st.node_off.ensure((size_t)st.count + new_hits + 1, s, true));
-      if (new_hits) {
-        count_launch();
-        k_compact<<<grid_for((size_t)n_chunks * 32, 256, 8192), 256, 0, s>>>(
-            st.chunk_hits.p, st.chunk_off.p, st.recs.p, cap, n_chunks, st.next_attempt, st.aid.p + st.count,
-            st.len.p + st.count);
-        HSAW_CK(cudaGetLastError());
-        HSAW_TRY(st.tmp64.ensure((size_t)new_hits + 1, s));
-        count_launch();
-        k_len_to_u64<<<grid_for(new_hits, 256, 4096), 256, 0, s>>>(st.len.p + st.count, new_hits, st.tmp64.p);
-        HSAW_CK(cudaGetLastError());
-        HSAW_TRY(exclusive_scan_u64(st.tmp64.p, new_hits, st.tmp64.p + new_hits, s));
-        count_launch();
-        k_offsets<<<grid_for((size_t)new_hits + 1, 256, 4096), 256, 0, s>>>(
-            st.tmp64.p, new_hits, st.total_nodes, st.node_off.p + st.count, st.tmp64.p + new_hits);
-        HSAW_CK(cudaGetLastError());
-        uint64_t added = 0;
-        HSAW_CK(cudaMemcpyAsync(&added, st.tmp64.p + new_hits, 8, cudaMemcpyDeviceToHost, s));
-        HSAW_CK(cudaStreamSynchronize(s));
-        const int64_t tot = st.total_nodes + (int64_t)added;
-        HSAW_TRY(st.nodes.ensure((size_t)tot, s, true));
-        HSAW_TRY(st.edges.ensure((size_t)tot, s, true));
-        if (pooled) {
-          pool_copy_launch(g, st, st.count, st.count + new_hits, s);
-        } else {
-          count_launch();
-          k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, P.k0, P.k1,
-                                                                       st.aid.p, st.len.p, st.node_off.p, st.count,
-                                                                       st.count + new_hits, st.nodes.p, st.edges.p);
-        }
-        HSAW_CK(cudaGetLastError());
-        st.total_nodes = tot;
-        st.count += new_hits;
-      }
-      st.next_attempt += batch;
-      break;
+    uint32_t new_hits = 0;
+    if (pool_ok && st.next_attempt < g.pool.attempts) {
+      // whole blocks of the index where the pool and the budget allow
+      const uint64_t B = 1ull << g.pool.shift;
+      uint64_t a1 = std::min<uint64_t>(g.pool.attempts, (st.next_attempt + batch + B - 1) / B * B);
+      a1 = std::min<uint64_t>(a1, st.next_attempt + (st.max_attempts - used));
+      batch = a1 - st.next_attempt;
+      HSAW_TRY(pool_hits(g, qd, st, st.next_attempt, a1, &new_hits, s));
+    } else {
+      batch = (batch + CHUNK - 1) / CHUNK * CHUNK;
+      HSAW_TRY(sample_window(g, qd, st, batch, &new_hits, s));
     }
+    if (new_hits) {
+      // walk offsets, then the hits' nodes and edges re-drawn from their attempt ids
+      HSAW_TRY(st.node_off.ensure((size_t)st.count + new_hits + 1, s, true));
+      HSAW_TRY(st.tmp64.ensure((size_t)new_hits + 1, s));
+      count_launch();
+      k_len_to_u64<<<grid_for(new_hits, 256, 4096), 256, 0, s>>>(st.len.p + st.count, new_hits, st.tmp64.p);
+      HSAW_CK(cudaGetLastError());
+      HSAW_TRY(exclusive_scan_u64(st.tmp64.p, new_hits, st.tmp64.p + new_hits, s));
+      count_launch();
+      k_offsets<<<grid_for((size_t)new_hits + 1, 256, 4096), 256, 0, s>>>(
+          st.tmp64.p, new_hits, st.total_nodes, st.node_off.p + st.count, st.tmp64.p + new_hits);
+      HSAW_CK(cudaGetLastError());
+      uint64_t added = 0;
+      HSAW_CK(cudaMemcpyAsync(&added, st.tmp64.p + new_hits, 8, cudaMemcpyDeviceToHost, s));
+      HSAW_CK(cudaStreamSynchronize(s));
+      const int64_t tot = st.total_nodes + (int64_t)added;
+      HSAW_TRY(st.nodes.ensure((size_t)tot, s, true));
+      HSAW_TRY(st.edges.ensure((size_t)tot, s, true));
+      count_launch();
+      k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, k0, k1, st.aid.p,
+                                                                   st.len.p, st.node_off.p, st.count,
+                                                                   st.count + new_hits, st.nodes.p, st.edges.p);
+      HSAW_CK(cudaGetLastError());
+      st.total_nodes = tot;
+      st.count += new_hits;
+    }
+    st.next_attempt += batch;
   }
   return HSAW_OK;
 }

@@ -9,6 +9,8 @@ namespace hsaw {
 struct QueryDev {
   uint32_t* s_bits = nullptr;     // n bits: v in V_I
   uint32_t* p32 = nullptr;        // n words or NULL (p == 1)
+  int32_t* s_list = nullptr;      // n_src node ids of V_I
+  int32_t n_src = 0;
   uint8_t* edge_removed = nullptr;  // m bytes or NULL
   uint8_t* node_removed = nullptr;  // n bytes or NULL
   uint64_t seed = 0;
@@ -37,6 +39,8 @@ struct Stream {
   DBuf<uint32_t> chunk_hits, chunk_off, ctrs;
   DBuf<uint2> recs;
   DBuf<uint64_t> tmp64;
+  DBuf<uint32_t> pbits;  // walk pool: one bit per attempt of a window
+  DBuf<uint64_t> pcnt;   // walk pool: entries per (source, block), then their prefix
   double hit_rate = 0.0;  // running estimate for launch sizing
   int64_t elem_range[2] = {0, 0};  // [node mode, edge mode]: element ids lie in [0, n) / [0, m)
   void release(cudaStream_t s);
@@ -76,9 +80,10 @@ hsaw_status cover_count(const Stream& st, hsaw_mode mode, int64_t first, int64_t
 // Walk pool (pool.cu).
 void pool_release(WalkPool& p);
 hsaw_status pool_build(Graph& g, uint64_t seed, uint64_t attempts, cudaStream_t s);
-void pool_scan_launch(const Graph& g, const QueryDev& qd, uint64_t a0, uint32_t n_attempts, uint32_t chunk,
-                      uint32_t cap, uint32_t* chunk_hits, uint2* recs, uint32_t* status, cudaStream_t s);
-void pool_copy_launch(const Graph& g, const Stream& st, int64_t h0, int64_t h1, cudaStream_t s);
+// Append to st (aid, len at st.count) the hits among attempts [a0, a1) (a1 <= pool.attempts),
+// in attempt order; *new_hits receives their number.
+hsaw_status pool_hits(const Graph& g, const QueryDev& qd, Stream& st, uint64_t a0, uint64_t a1, uint32_t* new_hits,
+                      cudaStream_t s);
 
 // Cancellation of the calling thread's current solve (set by the server's workers):
 // checked between sampler launches and between stopping-rule rounds.

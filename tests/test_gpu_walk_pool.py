@@ -1,8 +1,9 @@
 """Walk-pool reuse gives exactly the plain solver's results (GPU).
 
-A pool keeps attempt traces that do not depend on the query; queries with the pool's walk
-seed scan them for attempts inside the pool and sample the rest.  Every result here is
-compared with the same call on a graph without a pool.
+A pool indexes attempt traces that do not depend on the query (per block of 2^22 attempts,
+each node's list of attempts whose trace passes through it); queries with the pool's walk
+seed take their hits inside the pool from their sources' lists and sample the rest.  Every
+result here is compared with the same call on a graph without a pool.
 """
 import numpy as np
 import pytest
@@ -21,13 +22,16 @@ def pair(d):
     return plain, pooled
 
 
+POOL = (1 << 22) + (1 << 21) + 777  # two index blocks, the second one partial
+
+
 @pytest.fixture(scope="module")
 def c1():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     d = synth.workload_c1()
     plain, pooled = pair(d)
-    pooled.build_walk_pool(seed=4, attempts=1 << 22)
+    pooled.build_walk_pool(seed=4, attempts=POOL)
     return d, plain, pooled
 
 
@@ -52,17 +56,19 @@ def test_pooled_solves_match_plain(c1, mode):
     queries = [hs.Query(sources=d["sources"], mode=mode, k=10, n_hsaw=20_000, seed=4),
                hs.Query(sources=d["sources"], mode=mode, k=10, sampling=hs.HSAW_STOP_RULE, eps=0.1, seed=4),
                hs.Query(sources=d["sources"], p_fixed=p, mode=mode, k=20, n_hsaw=8_000, seed=4),
-               # needs attempts beyond the pool's 2^22: scans then samples
-               hs.Query(sources=d["sources"][:2], mode=mode, k=5, n_hsaw=5_000, seed=4),
+               # one source, hit rate ~0.17%: needs attempts beyond the pool (index, then sampler)
+               hs.Query(sources=d["sources"][:1], mode=mode, k=5, n_hsaw=15_000, seed=4),
                hs.Query(sources=d["sources"], mode=mode, k=10, n_hsaw=5_000, seed=5)]  # other seed: no pool
     for q in queries:
         same_solve(hs.hsaw_solve(pooled, q), hs.hsaw_solve(plain, q))
+    assert hs.hsaw_solve(pooled, queries[3])[2]["attempts"] > POOL
 
 
 def test_pooled_streams_match_plain(c1):
     d, plain, pooled = c1
     q = hs.Query(sources=d["sources"], k=1, seed=4)
-    for first in (0, 12345, (1 << 22) - 3000):
+    # windows inside the first block, across the block boundary, across the pool's end
+    for first in (0, 12345, (1 << 22) - 1000, POOL - 3000):
         same_prefix(hs.hsaw_sample(pooled, q, first, 3000).export(), hs.hsaw_sample(plain, q, first, 3000).export(),
                     3000)
     # residual graphs bypass the pool and still agree
