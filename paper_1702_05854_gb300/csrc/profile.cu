@@ -23,14 +23,39 @@ struct PhaseTimed {
 };
 static std::vector<PhaseTimed> g_phase;
 static uint64_t g_steps = 0, g_sampler_launches = 0, g_attempts = 0;
+// Timing events are recycled: creating two per phase in every worker thread of a server
+// costs more host time than the phases themselves.
+static std::vector<cudaEvent_t> g_free_events;
+
+static bool take_events(cudaEvent_t* a, cudaEvent_t* b) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_free_events.size() >= 2) {
+      *a = g_free_events.back();
+      g_free_events.pop_back();
+      *b = g_free_events.back();
+      g_free_events.pop_back();
+      return true;
+    }
+  }
+  if (cudaEventCreate(a) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaEventCreate(b) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(*a);
+    return false;
+  }
+  return true;
+}
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void* profile_begin(cudaStream_t s) {
   if (!g_enabled.load()) return nullptr;
   Timed* t = new Timed();
-  if (cudaEventCreate(&t->a) != cudaSuccess || cudaEventCreate(&t->b) != cudaSuccess) {
-    cudaGetLastError();
+  if (!take_events(&t->a, &t->b)) {
     delete t;
     return nullptr;
   }
@@ -53,8 +78,7 @@ void profile_end(void* token, cudaStream_t s, uint64_t attempts) {
 void* phase_begin(cudaStream_t s) {
   if (!g_enabled.load()) return nullptr;
   PhaseTimed* t = new PhaseTimed();
-  if (cudaEventCreate(&t->a) != cudaSuccess || cudaEventCreate(&t->b) != cudaSuccess) {
-    cudaGetLastError();
+  if (!take_events(&t->a, &t->b)) {
     delete t;
     return nullptr;
   }
@@ -86,13 +110,13 @@ extern "C" {
 hsaw_status hsaw_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto& t : g_timed) {
-    cudaEventDestroy(t.a);
-    cudaEventDestroy(t.b);
+    g_free_events.push_back(t.a);
+    g_free_events.push_back(t.b);
   }
   g_timed.clear();
   for (auto& t : g_phase) {
-    cudaEventDestroy(t.a);
-    cudaEventDestroy(t.b);
+    g_free_events.push_back(t.a);
+    g_free_events.push_back(t.b);
   }
   g_phase.clear();
   g_steps = g_sampler_launches = g_attempts = 0;

@@ -105,3 +105,21 @@ def test_allocation_failures_are_reported_and_recovered(c1):
     assert seen_nomem > 5
     g2 = hs.hsaw_graph_from_edges(d["n"], d["src"], d["dst"], d["w"])
     assert np.array_equal(hs.hsaw_solve(g2, q)[0], ref[0])
+
+
+def test_profile_counters_reset_and_results_unchanged(c1):
+    d, g, og = c1
+    q = hs.Query(sources=d["sources"], mode=hs.HSAW_EDGE, k=10, sampling=hs.HSAW_STOP_RULE, eps=0.2, seed=4)
+    hs.hsaw_profile_enable(False)
+    ref = hs.hsaw_solve(g, q)
+    for _ in range(3):  # repeated enables recycle the timing events
+        hs.hsaw_profile_enable(True)
+        got = hs.hsaw_solve(g, q)
+        p = hs.hsaw_profile_read()
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+        assert p["kernel_launches"] > 0 and p["sampler_launches"] >= 1 and p["sampler_ms"] > 0
+        assert p["sampler_steps"] == got[2]["steps"]
+        assert all(p["phase_ms"][k] > 0 for k in ("sampling", "counting", "greedy", "coverage"))
+    hs.hsaw_profile_enable(False)
+    p = hs.hsaw_profile_read()
+    assert p["kernel_launches"] == 0 and p["sampler_launches"] == 0 and p["phase_ms"]["greedy"] == 0
