@@ -180,7 +180,9 @@ class Graph:
         return self._h
 
     def build_walk_pool(self, seed: int, attempts: int, stream=None):
-        """Keep the query-independent traces of attempts [0, attempts) for walk seed `seed`."""
+        """Index the query-independent traces of attempts [0, attempts) for walk seed `seed`
+        (per node, the attempts whose trace passes through it); queries with that seed then
+        take their hits below `attempts` from their sources' lists."""
         _check(load().hsaw_graph_build_walk_pool(self._h, seed, attempts, _stream(stream)))
 
     def drop_walk_pool(self):
