@@ -274,6 +274,16 @@ def serve_queries(count, graphs_meta, min_sources, seed=5):
     return out
 
 
+def serve_pool_sizes(pool_attempts, ns):
+    """Walk-pool attempts per graph: in proportion to the graph's nodes (hit rates fall as
+    1/n for the same source-set sizes), whole index blocks of 2^22 attempts, the largest
+    graph getting pool_attempts (0: no pools)."""
+    if not pool_attempts:
+        return [0 for _ in ns]
+    n_max = max(ns)
+    return [max(1 << 22, (pool_attempts * n // n_max) >> 22 << 22) for n in ns]
+
+
 def run_serve_mode(args, hs, torch):
     scales = [int(x) for x in args.serve_scales.split(",")]
     gm, graphs = [], []
@@ -284,11 +294,7 @@ def run_serve_mode(args, hs, torch):
         gm.append((n, int(src.shape[0])))
     qs = serve_queries(args.serve_queries, gm, args.serve_min_sources)
     pool_attempts = int(args.serve_pool_attempts)
-    # pool sizes in proportion to the graph's nodes (hit rates fall as 1/n for the same
-    # source-set sizes), whole index blocks of 2^22 attempts, the largest graph getting
-    # --serve-pool-attempts
-    n_max = max(n for n, _ in gm)
-    pool_sizes = [max(1 << 22, (pool_attempts * n // n_max) >> 22 << 22) if pool_attempts else 0 for n, _ in gm]
+    pool_sizes = serve_pool_sizes(pool_attempts, [n for n, _ in gm])
     if pool_attempts:  # every query on a graph shares its walk seed, so traces can be reused
         for _, kw in qs:
             kw["seed"] = synth.SEED_WALKS

@@ -92,3 +92,19 @@ def test_pooled_unequal_weights_and_served(c1):
     srv.close()
     pooled.drop_walk_pool()
     same_solve(hs.hsaw_solve(pooled, q), ref)
+
+
+def test_pool_rebuild_drop_and_invalid(c1):
+    d = synth.workload_c1()
+    plain, pooled = pair(d)
+    q4 = hs.Query(sources=d["sources"], mode=hs.HSAW_NODE, k=10, n_hsaw=4_000, seed=4)
+    q9 = hs.Query(sources=d["sources"], mode=hs.HSAW_NODE, k=10, n_hsaw=4_000, seed=9)
+    with pytest.raises(hs.HsawError) as e:
+        pooled.build_walk_pool(seed=4, attempts=(1 << 32) + 1)
+    assert e.value.status == -1
+    pooled.build_walk_pool(seed=4, attempts=1 << 20)
+    pooled.build_walk_pool(seed=9, attempts=(1 << 21) + 5)  # replaces the seed-4 pool
+    for q in (q4, q9):                                      # seed 4: plain path; seed 9: pooled
+        same_solve(hs.hsaw_solve(pooled, q), hs.hsaw_solve(plain, q))
+    pooled.build_walk_pool(seed=9, attempts=0)              # zero attempts: no pool
+    same_solve(hs.hsaw_solve(pooled, q9), hs.hsaw_solve(plain, q9))
