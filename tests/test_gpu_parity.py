@@ -348,3 +348,27 @@ def test_stop_constants_and_check_match_oracle():
         ok1, e1 = hs.hsaw_check(c, cp, size, t, 0.1, 3137.84)
         ok2, e2 = oracle.check(c, cp, size, t, 0.1, 3137.84)
         assert ok1 == ok2 and (math.isnan(e1) and math.isnan(e2) or e1 == pytest.approx(e2, rel=1e-13))
+
+
+def test_solve_degenerate_cases():
+    """Every node a source (all walks have length 1: no edges to cover in eSI, only
+    zero-gain fills), the largest budget k = |C|, and a three-element candidate set."""
+    n, src, dst, w = random_tiny(4242, n=9, m=30)
+    g, og = both(n, src, dst, w)
+    S = np.arange(n, dtype=np.int32)
+    for mode, M in ((hs.HSAW_EDGE, len(src)), (hs.HSAW_NODE, n)):
+        for kw, okw in ((dict(n_hsaw=2_000), dict(n_hsaw=2_000)),
+                        (dict(sampling=hs.HSAW_STOP_RULE, eps=0.1), dict(stop_rule=True, eps=0.1))):
+            res = hs.hsaw_solve(g, hs.Query(sources=S, mode=mode, k=M, seed=11, **kw))
+            ores = oracle.solve(oracle.Query(og, S, seed=11), mode, M, **okw)
+            assert_solve_equal(res, ores)
+            if mode == hs.HSAW_EDGE:
+                assert np.array_equal(res[0], np.arange(M)) and not res[1].any()
+    # two sources, k = |C| over three candidate elements
+    S2 = np.array([0, 4], np.int32)
+    cm = np.zeros(n, np.uint8)
+    cm[[1, 5, 8]] = 1
+    res = hs.hsaw_solve(g, hs.Query(sources=S2, mode=hs.HSAW_NODE, k=3, n_hsaw=3_000, candidate_mask=cm, seed=2))
+    ores = oracle.solve(oracle.Query(og, S2, seed=2), oracle.MODE_NODE, 3, n_hsaw=3_000, cand_mask=cm)
+    assert_solve_equal(res, ores)
+    assert sorted(res[0].tolist()) == [1, 5, 8]
