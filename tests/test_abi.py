@@ -35,3 +35,70 @@ def test_binding_covers_every_declared_symbol():
 
 def test_built_for_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(hs.build.ARCH)
+
+
+# ------------------------------------------------------------------ declarations vs binding
+_SCALAR = {"int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64, "int32_t": ctypes.c_int32,
+           "uint32_t": ctypes.c_uint32, "int": ctypes.c_int, "double": ctypes.c_double, "size_t": ctypes.c_size_t,
+           "hsaw_mode": ctypes.c_int, "hsaw_sampling": ctypes.c_int}
+_OPAQUE = {"hsaw_graph", "hsaw_walks", "hsaw_server"}
+
+
+def _strip_comments(text):
+    return re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", text, flags=re.S))
+
+
+def declarations():
+    """name -> list of parameter type strings, from every HSAW_API prototype."""
+    text = _strip_comments(open(HEADER).read())
+    out = {}
+    for m in re.finditer(r"HSAW_API\s+[\w\s\*]+?\b(hsaw_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip()]
+        if params == ["void"]:
+            params = []
+        out[m.group(1)] = [re.sub(r"\s*\b\w+$", "", p) if not p.endswith("*") else p for p in params]
+    return out
+
+
+def _kind(ctype):
+    """'ptr' for pointers and opaque handles, else the ctypes scalar class."""
+    if ctype in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(ctype, type) and issubclass(ctype, ctypes._Pointer)):
+        return "ptr"
+    return ctype
+
+
+def test_binding_signatures_match_declarations():
+    decl = declarations()
+    assert len(decl) == len(declared_symbols())
+    for name, params in decl.items():
+        args = hs.SIGNATURES[name][1]
+        assert len(args) == len(params), (name, params, args)
+        for p, a in zip(params, args):
+            base = p.replace("const", "").strip()
+            if "*" in base or base in _OPAQUE:
+                assert _kind(a) == "ptr", (name, p, a)
+            else:
+                want = _SCALAR[base]
+                assert ctypes.sizeof(a) == ctypes.sizeof(want), (name, p, a)
+                assert (a(-1).value < 0) == (want(-1).value < 0) or want is ctypes.c_double, (name, p, a)
+
+
+def _struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    text = _strip_comments(open(HEADER).read())
+    body = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = re.sub(r"\[\d+\]", "", decl).strip()  # arrays: keep the name
+        if not decl:
+            continue
+        first, *more = decl.split(",")
+        fields.append(re.findall(r"\w+", first)[-1])
+        fields += [m.strip(" *") for m in more]
+    return fields
+
+
+def test_structs_match_declarations():
+    for cname, pyc in (("hsaw_query", hs.hsaw_query), ("hsaw_result", hs.hsaw_result),
+                       ("hsaw_profile", hs.hsaw_profile)):
+        assert _struct_fields(cname) == [f for f, _ in pyc._fields_], cname
