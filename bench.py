@@ -38,7 +38,7 @@ UNIT = "HSAW/s"
 BYTES_PER_STEP = 96  # three random 32-byte sectors per live-edge draw: node record, threshold, tail node
 # DRAM bytes per attempt of the sampler kernel from an ncu capture, keyed by the hash of
 # the sampler source it was taken on (the figure is void once the kernel changes).
-NCU_TRAFFIC = {"e2c49835baf4": 6565.0}  # 6 launches of 1.0-88.3 M attempts, 6,543-6,570 B each (profiles/)
+NCU_TRAFFIC = {"58b3cdf549d9": 6565.0}  # 6 launches of 1.0-88.3 M attempts, 6,543-6,570 B each (profiles/)
 
 
 def sampler_hash():

@@ -67,10 +67,13 @@ struct DBuf {  // grow-only device buffer
 // node and everything the next draw at u needs, so a walk makes one dependent DRAM access
 // per live-edge draw at equal-weight nodes (the tail's record is replicated per in-edge:
 // 32 B per edge of HBM for half the dependent latency and DRAM sectors per draw).
-// guide[e] (only when some node has unequal in-weights): for node v and bucket
-// b = floor(r * deg / in-sum) in [0, deg), guide[first(v) + b] = the live in-edge index of
+// Guide tables (only when some node has unequal in-weights): for node v and bucket
+// b = floor(r * deg / in-sum) in [0, deg), the guide entry is the live in-edge index j0 of
 // the smallest draw of the bucket, ceil(b * in-sum / deg); the answer for any r of the
 // bucket is at or after it (Chen & Asau's guide table), usually within a step or two.
+// grec[2p], grec[2p+1] (p = first(v) + b) hold the walk record of in-edge j0 with j0 in
+// the second half's third word, so a draw reads its candidate record directly (one
+// dependent access, like equal weights) and steps through erec only past it.
 // Walk pool (query-independent traces, kept as an inverted index): for walk seed `seed`,
 // trace a (a < attempts) is attempt a's walk ignoring sources - its nodes until no live
 // in-edge or a detected cycle.  A query's HSAW of attempt a is the trace's prefix up to its
@@ -96,7 +99,7 @@ struct Graph {
   uint4* node = nullptr;
   uint2* edge = nullptr;
   uint4* erec = nullptr;
-  uint32_t* guide = nullptr;
+  uint4* grec = nullptr;
   int64_t* input_index = nullptr;  // CSR position -> input edge index (NULL = identity)
   int device = 0;
 };

@@ -192,6 +192,26 @@ __global__ void k_guide(const uint4* __restrict__ node, const uint2* __restrict_
   if (cnt) atomicAdd(n_unequal, cnt);
 }
 
+// Bucket records of the nodes with unequal in-weights (see Graph::grec); one warp per node.
+__global__ void k_guide_records(const uint4* __restrict__ node, const uint32_t* __restrict__ guide, int64_t n,
+                                const uint4* __restrict__ erec, uint4* __restrict__ grec) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const uint4 nd = node[v];
+    if (nd.y == 0 || nd.z != 0 || nd.w == 0) continue;
+    for (uint32_t b = lane; b < nd.y; b += 32) {
+      const size_t p = (size_t)nd.x + b;
+      const uint32_t j0 = guide[p];
+      const size_t e0 = (size_t)nd.x + j0;
+      grec[2 * p] = erec[2 * e0];
+      uint4 hi = erec[2 * e0 + 1];
+      hi.z = j0;
+      grec[2 * p + 1] = hi;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host
 static hsaw_status check_err(uint32_t* d_err, cudaStream_t s) {
   uint32_t h = 0;
@@ -230,9 +250,9 @@ static void destroy_graph(Graph& g) {
   if (g.edge) cudaFree(g.edge);
   if (g.input_index) cudaFree(g.input_index);
   if (g.erec) cudaFree(g.erec);
-  if (g.guide) cudaFree(g.guide);
+  if (g.grec) cudaFree(g.grec);
   g.erec = nullptr;
-  g.guide = nullptr;
+  g.grec = nullptr;
   g.node = nullptr;
   g.edge = nullptr;
   g.input_index = nullptr;
@@ -275,19 +295,32 @@ static hsaw_status finish_graph(Graph& g, uint32_t* row_start, uint32_t* d_err, 
     count_launch();
     k_walk_records<<<grid_for(g.m, 256, 1u << 16), 256, 0, s>>>(g.edge, g.node, g.m, g.erec);
     HSAW_CK(cudaGetLastError());
-    // guide tables, kept only when some node has unequal in-weights
-    HSAW_CK(cudaMalloc((void**)&g.guide, (size_t)g.m * sizeof(uint32_t)));
+    // guide tables and their bucket records, kept only when some node has unequal
+    // in-weights (the guide itself is a temporary)
+    uint32_t* guide = nullptr;
+    HSAW_TRY(dmalloc((void**)&guide, (size_t)g.m * sizeof(uint32_t), s));
     HSAW_CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
     count_launch();
-    k_guide<<<grid_for((size_t)n * 32, 256, 1u << 20), 256, 0, s>>>(g.node, g.edge, n, g.guide, d_err);
-    HSAW_CK(cudaGetLastError());
+    k_guide<<<grid_for((size_t)n * 32, 256, 1u << 20), 256, 0, s>>>(g.node, g.edge, n, guide, d_err);
     uint32_t unequal = 0;
-    HSAW_CK(cudaMemcpyAsync(&unequal, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    HSAW_CK(cudaStreamSynchronize(s));
-    if (unequal == 0) {
-      cudaFree(g.guide);
-      g.guide = nullptr;
+    hsaw_status st = HSAW_OK;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&unequal, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = fail(HSAW_E_DEVICE, "graph: guide tables failed");
+    if (st == HSAW_OK && unequal) {
+      if (cudaMalloc((void**)&g.grec, (size_t)g.m * 2 * sizeof(uint4)) != cudaSuccess) {
+        cudaGetLastError();
+        g.grec = nullptr;
+        st = fail(HSAW_E_NOMEM, "graph: guide records do not fit in device memory");
+      } else {
+        count_launch();
+        k_guide_records<<<grid_for((size_t)n * 32, 256, 1u << 20), 256, 0, s>>>(g.node, guide, n, g.erec, g.grec);
+        if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "graph: guide records failed");
+      }
     }
+    dfree(guide, s);
+    HSAW_TRY(st);
   }
   return HSAW_OK;
 }

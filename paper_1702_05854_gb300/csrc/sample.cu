@@ -28,7 +28,7 @@ struct SampleParams {
   const uint4* __restrict__ node;
   const uint2* __restrict__ edge;
   const uint4* __restrict__ erec;
-  const uint32_t* __restrict__ guide;
+  const uint4* __restrict__ grec;
   const uint32_t* __restrict__ s_bits;
   const uint32_t* __restrict__ p32;
   const uint8_t* __restrict__ edge_removed;
@@ -102,14 +102,18 @@ __global__ void __launch_bounds__(256, 6) k_sample(SampleParams P) {
             e = rec.x + x.x / rec.z;
             ra = __ldg(&P.erec[2 * (size_t)e]);
             rb = __ldg(&P.erec[2 * (size_t)e + 1]);
-          } else {  // guide table, then step through the walk records (they carry thr)
-            e = rec.x + __ldg(&P.guide[rec.x + guide_bucket(x.x, rec.y, rec.w)]);
-            rb = __ldg(&P.erec[2 * (size_t)e + 1]);
-            while (x.x >= rb.y) {
-              ++e;
-              rb = __ldg(&P.erec[2 * (size_t)e + 1]);
+          } else {  // the bucket's candidate record, then step through the walk records
+            const size_t gp = 2 * ((size_t)rec.x + guide_bucket(x.x, rec.y, rec.w));
+            ra = __ldg(&P.grec[gp]);
+            rb = __ldg(&P.grec[gp + 1]);
+            e = rec.x + rb.z;
+            if (x.x >= rb.y) {
+              do {
+                ++e;
+                rb = __ldg(&P.erec[2 * (size_t)e + 1]);
+              } while (x.x >= rb.y);
+              ra = __ldg(&P.erec[2 * (size_t)e]);
             }
-            ra = __ldg(&P.erec[2 * (size_t)e]);
           }
         }
         const bool suspect = (sw >> (v & 31)) & 1u;
@@ -328,7 +332,7 @@ static SampleParams make_params(const Graph& g, const QueryDev& qd) {
   P.node = g.node;
   P.edge = g.edge;
   P.erec = g.erec;
-  P.guide = g.guide;
+  P.grec = g.grec;
   P.s_bits = qd.s_bits;
   P.p32 = qd.p32;
   P.edge_removed = qd.edge_removed;
@@ -608,7 +612,7 @@ extern "C" hsaw_status hsaw_sample_hits_static(hsaw_graph g, const uint32_t* sus
   P.node = G.node;
   P.edge = G.edge;
   P.erec = G.erec;
-  P.guide = G.guide;
+  P.grec = G.grec;
   P.s_bits = suspect_bits;
   P.n = (uint32_t)G.n;
   P.k0 = (uint32_t)seed;
