@@ -5,8 +5,7 @@ computes (``oracle.c``; each C function cites the paper passage it follows).  On
 tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may use it;
 the product library never imports it and shares no code with it.
 
-Pins: see the header of ``oracle.c`` and ``tests/test_oracle_*.py``.  The epsilon_t
-expression of the Check step is parity unpinned (the paper prints no worked value).
+Pins: see the header of ``oracle.c`` and ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
 

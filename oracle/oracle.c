@@ -22,9 +22,9 @@
  *   greedy      - brute-force optimal max-coverage on tiny inputs (1-1/e bound),
  *                 exact optimum for k=1, tie and zero-gain rules on hand-built cases.
  *   stop rule   - log-binomial against exact integer binomials; the t_max definition
- *                 as a doubling bound; Check's monotonicity and special cases.
- *                 The epsilon_t expression itself is parity unpinned (the paper prints
- *                 no worked value).
+ *                 as a doubling bound; Check's monotonicity and special cases; the
+ *                 epsilon_t expression against hand-evaluated cases (t = 1, 3, 5) and
+ *                 against the closed-form coverage at which Check starts to pass.
  */
 #include <math.h>
 #include <stdint.h>

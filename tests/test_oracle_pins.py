@@ -377,6 +377,72 @@ def test_check_behaviour():
     assert et >= 0.2 * (1 - 1 / math.e - 0.1)
 
 
+# Check (Alg. 5) evaluated by hand.  With |R'_t| = L 2^(t-1) (L = ceil(Lambda)) the
+# quantity under eps_2's root is rho = |R'_t| (1 + eps) / (2^(t-1) c'), so
+#   eps_2 = eps sqrt(rho),   eps_3 = eps sqrt(rho (1 - 1/e - eps) / (1 + eps/3)),
+#   eps_t = ((c / c') (1 + eps_2) - 1)(1 - 1/e - eps) + (1 - 1/e) eps_3,
+# using eps_1 + eps_2 + eps_1 eps_2 = (1 + eps_1)(1 + eps_2) - 1 and 1 + eps_1 = c / c'
+# (the factorisation the paper's proof of Lemma "e2e" part (C) uses).  The numbers below
+# were worked out digit by digit (25-digit arithmetic) and are literals here.
+CHECK_CASES = [
+    # eps, t, |R'_t|, c', c, expected eps_t
+    # (a) t = 3, L = 1000: rho = 4000 * 1.5 / (4 * 1500) = 1, eps_2 = 0.5, eps_1 = 1800/1500 - 1 = 0.2,
+    #     gap = 1 - 1/e - 0.5 = 0.1321205588285577, eps_3 = 0.5 sqrt(gap / (7/6))
+    #     = 0.5 sqrt(0.1132461932816209) = 0.5 * 0.3365207174627156 = 0.1682603587313578,
+    #     eps_t = 1.2 * 1.5 - 1 = 0.8 times gap = 0.1056964470628461
+    #           + (1 - 1/e) eps_3 = 0.6321205588285577 * 0.1682603587313578 = 0.1063608319899595
+    #           = 0.2120572790528056
+    (0.5, 3, 4000, 1500, 1800, 0.2120572790528056),
+    # (b) t = 1, L = 5000: rho = 5000 * 1.1 / 4400 = 1.25, eps_2 = 0.1 sqrt(1.25) = 0.1118033988749895,
+    #     eps_1 = 4840/4400 - 1 = 0.1, gap = 0.5321205588285577,
+    #     eps_3 = 0.1 sqrt(1.25 gap / (31/30)) = 0.1 sqrt(0.6436942243893843) = 0.08023055679660863,
+    #     eps_t = (0.1 + 1.1 * 0.1118033988749895) gap = 0.1186542316799765
+    #           + 0.6321205588285577 * 0.08023055679660863 = 0.05071538439739858
+    #           = 0.1693696160773750
+    (0.1, 1, 5000, 4400, 4840, 0.1693696160773750),
+    # (c) t = 5, L = 4675 (C3's Lambda rounded up): |R'_5| = 4675 * 16 = 74800, c' = 41140,
+    #     rho = 74800 * 1.1 / (16 * 41140) = 0.125, eps_2 = 0.1 sqrt(0.125) = 0.03535533905932738,
+    #     eps_1 = 44880/41140 - 1 = 1/11, eps_3 = 0.1 sqrt(0.125 gap / (31/30))
+    #     = 0.1 sqrt(0.06436942243893843) = 0.02537112974207858,
+    #     eps_t = (1/11 + (12/11) 0.03535533905932738) gap = 0.06889819928749333
+    #           + 0.6321205588285577 * 0.02537112974207858 = 0.01603761271067455
+    #           = 0.08493581199816789
+    (0.1, 5, 74800, 41140, 44880, 0.08493581199816789),
+]
+
+
+@pytest.mark.parametrize("eps,t,size,cp,c,want", CHECK_CASES)
+def test_check_hand_evaluated(eps, t, size, cp, c, want):
+    """eps_t of Alg. 5 equals hand-evaluated values; the call passes iff eps_t <= eps.
+    A dropped eps_1 eps_2 term moves (a) by 0.013, (c) by 0.0017; 2^t in place of 2^(t-1)
+    moves eps_2 by a factor sqrt(2); swapping (1 - 1/e) and (1 - 1/e - eps) moves (a) by
+    0.06.  Each is far outside the 1e-12 tolerance."""
+    ok, et = oracle.check(c, cp, size, t, eps, 1.0)
+    assert et == pytest.approx(want, rel=1e-12, abs=0)
+    assert ok == (want <= eps)
+
+
+@pytest.mark.parametrize("eps,t,eps1", [(0.1, 2, 0.0), (0.1, 6, 0.05), (0.2, 3, 0.1), (0.3, 4, 0.2)])
+def test_check_threshold_closed_form(eps, t, eps1):
+    """Solving eps_t = eps for the verification coverage c' at a fixed ratio c / c' = 1 + eps_1
+    (a closed form, not the oracle's expression): with s = sqrt(L (1 + eps) / c'),
+        eps_t = eps_1 g + eps s [(1 + eps_1) g + (1 - 1/e) sqrt(g / (1 + eps/3))],  g = 1 - 1/e - eps,
+    so Check passes exactly when c' >= c*' = L (1 + eps) / s*^2 with
+        s* = (eps - eps_1 g) / (eps [(1 + eps_1) g + (1 - 1/e) sqrt(g / (1 + eps/3))])."""
+    L = 4675
+    size = L * 2 ** (t - 1)
+    g = 1 - 1 / math.e - eps
+    s_star = (eps - eps1 * g) / (eps * ((1 + eps1) * g + (1 - 1 / math.e) * math.sqrt(g / (1 + eps / 3))))
+    cp_star = L * (1 + eps) / s_star ** 2
+    assert cp_star < size  # a coverage the round can reach
+    for f, expect in ((1 + 1e-9, True), (1 - 1e-9, False)):
+        cp = cp_star * f
+        ok, et = oracle.check((1 + eps1) * cp, cp, size, t, eps, 1.0)
+        assert ok == expect, (f, et)
+    ok, et = oracle.check((1 + eps1) * cp_star, cp_star, size, t, eps, 1.0)
+    assert et == pytest.approx(eps, rel=1e-12)
+
+
 # ----------------------------------------------------------------------------- end-to-end quality
 @pytest.mark.parametrize("gseed", list(range(6)))
 def test_solve_quality_against_bruteforce(gseed):
