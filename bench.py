@@ -36,15 +36,21 @@ METRIC = "HSAWs/s at 1B edges (eSI stop-rule solve, R-MAT scale 26)"
 METRIC_OTHER = {"c2": "HSAWs/s (nSI R-MAT 20 random LT, N = 10 M)", "c1": "HSAWs/s (eSI Chung-Lu 16 K, N = 200 K)"}
 UNIT = "HSAW/s"
 BYTES_PER_STEP = 96  # three random 32-byte sectors per live-edge draw: node record, threshold, tail node
-# DRAM bytes per attempt of the sampler kernel from an ncu capture, keyed by the hash of
-# the sampler source it was taken on (the figure is void once the kernel changes).
-NCU_TRAFFIC = {"58b3cdf549d9": 6565.0}  # 6 launches of 1.0-88.3 M attempts, 6,543-6,570 B each (profiles/)
+# DRAM bytes (read + write) per live-edge draw of the sampler kernel from an ncu capture,
+# keyed by (hash of the kernel's source, workload).  A workload without a capture of the
+# current kernel reports traffic = null.
+NCU_TRAFFIC = {}
 
 
 def sampler_hash():
+    """Hash of k_sample's own source text and the device helpers it calls (common.cuh)."""
+    csrc = os.path.join(ROOT, "paper_1702_05854_gb300", "csrc")
+    src = open(os.path.join(csrc, "sample.cu")).read()
+    i = src.index("template <bool HAS_P, bool HAS_REM>\n__global__ void __launch_bounds__(256, 6) k_sample")
+    j = src.index("\n}\n", i)
     h = hashlib.sha1()
-    for f in ("sample.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1702_05854_gb300", "csrc", f), "rb").read())
+    h.update(src[i:j].encode())
+    h.update(open(os.path.join(csrc, "common.cuh"), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -507,9 +513,9 @@ def main():
     bytes_per_launch = BYTES_PER_STEP * prof["sampler_steps"] / launches
     achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     traffic = None
-    per_attempt = NCU_TRAFFIC.get(sampler_hash())
-    if per_attempt is not None:
-        traffic = per_attempt * prof["sampler_attempts"] / launches
+    per_draw = NCU_TRAFFIC.get((sampler_hash(), d["name"]))
+    if per_draw is not None:
+        traffic = per_draw * prof["sampler_steps"] / launches
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_sample", "peak_source": "measured" if peaks else "fallback",
                 "sampler_share_of_step": prof["sampler_ms"] / 1e3 / elapsed,

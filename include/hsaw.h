@@ -236,9 +236,13 @@ HSAW_API hsaw_status hsaw_classify(hsaw_graph g, const hsaw_query* q, uint64_t f
                           int8_t* outcome_dev, int32_t* length_dev, void* stream);
 
 /* ------------------------------------------------------------------ allocation-free sampling
- * The paper has no counterpart to this call; it exists for callers that cannot allocate
- * device memory: code running while a CUDA stream is being captured into a graph, or a
- * host framework that owns every device allocation and forbids others.
+ * The paper has no counterpart to this call.  It is for callers that must not allocate
+ * device memory once they are running: a host framework that owns every device
+ * allocation through its own pool and forbids others (a second allocator would fragment
+ * or exceed the budget it plans for), and latency-bound loops in which cudaMalloc and
+ * cudaFree are ruled out because they can synchronise the whole device and stall the
+ * other streams.  Such a caller passes its own input and output buffers; the scratch the
+ * sampler needs lives in the library itself.
  *
  * hsaw_sample_hits_static: the hits among attempts [first_attempt, first_attempt +
  *   n_attempts) of graph g, in increasing attempt id: aid_out[i] (device, uint64) and
@@ -249,10 +253,13 @@ HSAW_API hsaw_status hsaw_classify(hsaw_graph g, const hsaw_query* q, uint64_t f
  *   static array of the library that every GPU loading the library keeps until exit.
  *   Errors: HSAW_E_INVALID for n_attempts outside [0, HSAW_STATIC_MAX_ATTEMPTS], NULL
  *   arguments, or more hits than out_cap (then *n_hits is set and nothing is written).
+ *   HSAW_E_DEVICE when the current CUDA device is not the graph's device.
  *   The first call on a device looks up the scratch's device address (set-up); make it
- *   before any stream capture.  Every call shares the one scratch array: calls that
- *   overlap on the GPU (other threads or streams) race and must be serialised by the
- *   caller.  The call synchronises `stream` before it returns. */
+ *   before any stream capture.  Every call shares the one scratch array, which keeps the
+ *   last call's contents (the call clears what must start at zero): calls that overlap
+ *   on the GPU (other threads or streams) race and must be serialised by the caller.
+ *   The call synchronises `stream` (it reads the hit count back to the host) before it
+ *   returns. */
 #define HSAW_STATIC_MAX_ATTEMPTS (1u << 18)
 HSAW_API hsaw_status hsaw_sample_hits_static(hsaw_graph g, const uint32_t* suspect_bits, uint64_t seed,
                                              uint64_t first_attempt, int64_t n_attempts, uint64_t* aid_out,

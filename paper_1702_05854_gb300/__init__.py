@@ -408,12 +408,21 @@ def hsaw_sample_hits_static(graph: Graph, suspect_bits, seed: int, first_attempt
                             len_out, stream=None) -> int:
     """Allocation-free hit search over an attempt range (see include/hsaw.h).
 
-    suspect_bits, aid_out (int64 view of uint64) and len_out (int32 view of uint32) are
-    caller-owned torch CUDA tensors; returns the number of hits written."""
+    suspect_bits (int32 view of uint32, at least ceil(n / 32) words), aid_out (int64 view
+    of uint64) and len_out (int32 view of uint32) are caller-owned contiguous torch CUDA
+    tensors; returns the number of hits written.  The output capacity is the shorter of
+    the two output tensors."""
+    import torch
+    for name, t, dt in (("suspect_bits", suspect_bits, torch.int32), ("aid_out", aid_out, torch.int64),
+                        ("len_out", len_out, torch.int32)):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == dt):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of {dt}")
+    if suspect_bits.numel() < (graph.n + 31) // 32:
+        raise ValueError("suspect_bits must hold ceil(n / 32) words")
     n = _i64()
+    cap = min(int(aid_out.numel()), int(len_out.numel()))
     _check(load().hsaw_sample_hits_static(graph.handle, _ptr(suspect_bits), seed, first_attempt, n_attempts,
-                                          _ptr(aid_out), _ptr(len_out), int(aid_out.numel()), ctypes.byref(n),
-                                          _stream(stream)))
+                                          _ptr(aid_out), _ptr(len_out), cap, ctypes.byref(n), _stream(stream)))
     return int(n.value)
 
 

@@ -604,10 +604,13 @@ extern "C" hsaw_status hsaw_sample_hits_static(hsaw_graph g, const uint32_t* sus
   if (n_attempts < 0 || n_attempts > (int64_t)HSAW_STATIC_MAX_ATTEMPTS)
     return fail(HSAW_E_INVALID, "static sampler: n_attempts must be in [0, HSAW_STATIC_MAX_ATTEMPTS]");
   if (n_attempts == 0) return HSAW_OK;
+  const Graph& G = g->g;
+  int cur_dev = -1;
+  HSAW_CK(cudaGetDevice(&cur_dev));
+  if (cur_dev != G.device) return fail(HSAW_E_DEVICE, "static sampler: the current device is not the graph's device");
   StaticScratch* sc = nullptr;
   HSAW_TRY(static_scratch(&sc));
   cudaStream_t s = (cudaStream_t)stream;
-  const Graph& G = g->g;
   SampleParams P{};
   P.node = G.node;
   P.edge = G.edge;

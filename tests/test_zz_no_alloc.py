@@ -1,8 +1,9 @@
 """The allocation-free sampler entry point agrees with the allocating one.
 
-hsaw_sample_hits_static serves callers that may not allocate device memory (stream
-capture, frameworks that own every allocation).  Its scratch is a static device array
-shared by every call, so this test makes two calls in a row on the same array and
+hsaw_sample_hits_static serves callers that must not allocate device memory while they
+run (a framework that owns every device allocation through its own pool, or a loop that
+cannot afford cudaMalloc's device-wide synchronisation).  Its scratch is a static device
+array shared by every call, so this test makes two calls in a row on the same array and
 checks each against hsaw_sample, the entry point that allocates its own workspace.
 The file is named to run last: if it fails, every other test has already run.
 """
