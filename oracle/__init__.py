@@ -72,9 +72,12 @@ def _load():
             L.oracle_walks_attempts.argtypes = [p]; L.oracle_walks_attempts.restype = u64
             L.oracle_walks_steps.argtypes = [p]; L.oracle_walks_steps.restype = u64
             L.oracle_walks_export.argtypes = [p, p, p, p, p]
+            L.oracle_walks_append.argtypes = [p, p, u64, i64]; L.oracle_walks_append.restype = ctypes.c_int
             L.oracle_histogram.argtypes = [p, ctypes.c_int, i64, i64, i64, p]
             L.oracle_coverage.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i32]; L.oracle_coverage.restype = i64
             L.oracle_greedy.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i32, p, p]; L.oracle_greedy.restype = ctypes.c_int
+            L.oracle_greedy_lists.argtypes = [p, ctypes.c_int, i64, i64, i64, p, i32, p, p]
+            L.oracle_greedy_lists.restype = ctypes.c_int
             L.oracle_stop_constants.argtypes = [i64, i32, dbl, dbl, p]
             L.oracle_check.argtypes = [dbl, dbl, dbl, ctypes.c_int, dbl, dbl, ctypes.POINTER(dbl)]
             L.oracle_check.restype = ctypes.c_int
@@ -214,6 +217,7 @@ class Stream:
     def __init__(self, query: Query, first_aid: int = 0):
         self.query = query
         self._h = _load().oracle_walks_new(first_aid)
+        self._next = first_aid
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -222,9 +226,40 @@ class Stream:
             self._h = None
 
     def extend(self, want_hits: int, max_attempts: int = 1 << 62):
+        a0 = self.attempts
         rc = _load().oracle_stream_extend(self.query._h, self._h, want_hits, max_attempts)
         if rc != 0:
             raise RuntimeError(f"oracle stream failed ({rc})")
+        self._next += self.attempts - a0
+        return self
+
+    def extend_threads(self, want_hits: int, threads: int, max_attempts: int = 1 << 62, chunk: int = 1 << 16):
+        """extend() with the attempts examined by `threads` host threads in consecutive
+        ranges of `chunk` attempts, joined in attempt order: the same walks as extend()
+        (attempts are independent, Alg. 3).  Harness only; the oracle's arithmetic is the
+        per-attempt code that extend() runs.  `steps` covers whole ranges only."""
+        import concurrent.futures as cf
+        L = _load()
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            while len(self) < want_hits and max_attempts > 0:
+                firsts, parts = [], []
+                for _ in range(threads):
+                    if max_attempts <= 0:
+                        break
+                    c = min(chunk, max_attempts)
+                    firsts.append((self._next + sum(x[1] for x in firsts), c))
+                    max_attempts -= c
+                parts = [Stream(self.query, f) for f, _ in firsts]
+                list(ex.map(lambda pc: pc[0].extend(1 << 62, pc[1]), zip(parts, [c for _, c in firsts])))
+                for part, (f, c) in zip(parts, firsts):
+                    need = want_hits - len(self)
+                    cut = need <= len(part)
+                    rc = L.oracle_walks_append(self._h, part._h, f, need if cut else -1)
+                    if rc != 0:
+                        raise RuntimeError(f"oracle stream join failed ({rc})")
+                    self._next = int(part.export().aid[need - 1]) + 1 if cut else f + c
+                    if len(self) >= want_hits:
+                        break
         return self
 
     def __len__(self):
@@ -258,11 +293,14 @@ class Stream:
         T = np.ascontiguousarray(T, np.int64)
         return int(_load().oracle_coverage(self._h, mode, first, count, M, _ptr(T), T.shape[0]))
 
-    def greedy(self, mode, first, count, M, k, cand_mask=None):
+    def greedy(self, mode, first, count, M, k, cand_mask=None, kept_gains=False):
+        """Greedy (Alg. 4 / 7): gains recounted every round, or (kept_gains) kept and
+        decremented as walks are covered; both return the same picks."""
         ids = np.empty(k, np.int64)
         gains = np.empty(k, np.uint32)
         cm = None if cand_mask is None else np.ascontiguousarray(cand_mask, np.uint8)
-        rc = _load().oracle_greedy(self._h, mode, first, count, M, _ptr(cm), k, _ptr(ids), _ptr(gains))
+        f = _load().oracle_greedy_lists if kept_gains else _load().oracle_greedy
+        rc = f(self._h, mode, first, count, M, _ptr(cm), k, _ptr(ids), _ptr(gains))
         if rc != 0:
             raise ValueError(f"oracle greedy failed ({rc})")
         return ids, gains

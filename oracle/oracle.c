@@ -369,6 +369,30 @@ int oracle_stream_extend(const oracle_ctx* c, oracle_walks* W, int64_t want_hits
   return rc;
 }
 
+/* Append to W the walks of `part`, a stream that starts at W's next attempt id (the same
+ * query examined over a later, disjoint attempt range), keeping at most `limit` of them
+ * (limit < 0: all).  When `part` holds at least `limit` walks, W ends after the attempt of
+ * its limit-th walk, exactly as if W had been extended attempt by attempt to that many walks.  Lets a
+ * caller examine consecutive attempt ranges independently (Alg. 3's attempts are
+ * independent) and join them in attempt order.  Returns 0, -1 (part does not start at
+ * W's next attempt) or -4 (out of memory). */
+int oracle_walks_append(oracle_walks* W, const oracle_walks* part, uint64_t part_first, int64_t limit) {
+  if (part_first != W->next_aid) return -1;
+  const int cut = limit >= 0 && part->count >= limit;
+  const int64_t take = cut ? limit : part->count;
+  for (int64_t j = 0; j < take; ++j) {
+    int64_t b = part->node_off[j], e = part->node_off[j + 1];
+    int rc = walks_push(W, part->aid[j], part->nodes + b, part->edges + (b - j), e - b);
+    if (rc) return rc;
+  }
+  uint64_t next = part->next_aid;
+  if (cut) next = take > 0 ? part->aid[take - 1] + 1 : part_first;
+  else W->steps += part->steps; /* draws are known only for a part appended whole */
+  W->attempts += next - W->next_aid;
+  W->next_aid = next;
+  return 0;
+}
+
 /* Classify the attempts [first, first+count) one by one: writes the outcome code of each
  * attempt and the length of each walk (sampled-parity checks at full size). */
 void oracle_classify(const oracle_ctx* c, uint64_t first, int64_t count, int8_t* outcome, int32_t* length) {
@@ -497,6 +521,93 @@ int oracle_greedy(const oracle_walks* W, int mode, int64_t first, int64_t count,
     }
   }
   free(covered); free(picked); free(gain); free(touched);
+  return 0;
+}
+
+/* =====================================================================================
+ * The same greedy (Alg. 4 / Alg. 7, same tie and zero-gain rules), with the marginal
+ * gains kept instead of recounted: gain[x] = number of not-yet-covered walks that contain
+ * x.  It starts as the occurrence count, and when a pick covers walk j, every element of
+ * R_j loses that walk, so its gain drops by one.  Each round is a scan of the touched
+ * elements in increasing id (strict > keeps the smallest id on ties).  For streams too
+ * large for the recounting form; it must return exactly what oracle_greedy returns.
+ * ===================================================================================== */
+int oracle_greedy_lists(const oracle_walks* W, int mode, int64_t first, int64_t count, int64_t M,
+                        const uint8_t* cand_mask, int32_t k, int64_t* ids, uint32_t* gains) {
+  int64_t n_cand = 0;
+  for (int64_t x = 0; x < M; ++x) n_cand += (!cand_mask || cand_mask[x]) ? 1 : 0;
+  if (k < 1 || k > n_cand) return -1;
+  /* walks of each element (counting sort by element id) */
+  int64_t* off = (int64_t*)calloc((size_t)M + 1, sizeof(int64_t));
+  uint8_t* picked = (uint8_t*)calloc((size_t)(M ? M : 1), 1);
+  uint8_t* covered = (uint8_t*)calloc((size_t)(count ? count : 1), 1);
+  if (!off || !picked || !covered) { free(off); free(picked); free(covered); return -4; }
+  int64_t total = 0;
+  for (int64_t j = 0; j < count; ++j) {
+    int64_t l;
+    const int32_t* x = walk_elems(W, mode, first + j, &l);
+    for (int64_t i = 0; i < l; ++i) off[x[i] + 1]++;
+    total += l;
+  }
+  /* the touched elements in increasing id: element tid[t] has gain tgain[t] and is still
+     available (a candidate, not picked) iff tavail[t]; rank[x] = t */
+  int64_t nt = 0;
+  for (int64_t x = 0; x < M; ++x) nt += off[x + 1] ? 1 : 0;
+  int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(total ? total : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M ? M : 1));
+  int64_t* rank = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M ? M : 1));
+  int64_t* tid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt ? nt : 1));
+  uint32_t* tgain = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(nt ? nt : 1));
+  uint8_t* tavail = (uint8_t*)malloc((size_t)(nt ? nt : 1));
+  if (!list || !fill || !rank || !tid || !tgain || !tavail) {
+    free(off); free(picked); free(covered); free(list); free(fill); free(rank); free(tid); free(tgain); free(tavail);
+    return -4;
+  }
+  int64_t t = 0;
+  for (int64_t x = 0; x < M; ++x) {
+    const int64_t c = off[x + 1];
+    if (c) {
+      tid[t] = x;
+      tgain[t] = (uint32_t)c;
+      tavail[t] = (!cand_mask || cand_mask[x]) ? 1 : 0;
+      rank[x] = t++;
+    }
+  }
+  for (int64_t x = 0; x < M; ++x) off[x + 1] += off[x];
+  for (int64_t x = 0; x < M; ++x) fill[x] = off[x];
+  for (int64_t j = 0; j < count; ++j) {
+    int64_t l;
+    const int32_t* x = walk_elems(W, mode, first + j, &l);
+    for (int64_t i = 0; i < l; ++i) list[fill[x[i]]++] = j;
+  }
+  for (int32_t round = 0; round < k; ++round) {
+    int64_t best_t = -1;
+    uint32_t best_gain = 0;
+    for (int64_t u = 0; u < nt; ++u)
+      if (tavail[u] && tgain[u] > best_gain) { best_t = u; best_gain = tgain[u]; }
+    int64_t best;
+    if (best_t < 0) { /* every remaining gain is zero: smallest unpicked candidate */
+      best = -1;
+      for (int64_t x = 0; x < M; ++x)
+        if (!picked[x] && (!cand_mask || cand_mask[x])) { best = x; break; }
+      best_gain = 0;
+    } else {
+      best = tid[best_t];
+    }
+    ids[round] = best;
+    gains[round] = best_gain;
+    picked[best] = 1;
+    if (off[best + 1] > off[best]) tavail[rank[best]] = 0;
+    for (int64_t q = off[best]; q < off[best + 1]; ++q) {
+      int64_t j = list[q];
+      if (covered[j]) continue;
+      covered[j] = 1;
+      int64_t l;
+      const int32_t* x = walk_elems(W, mode, first + j, &l);
+      for (int64_t i = 0; i < l; ++i) tgain[rank[x[i]]]--;
+    }
+  }
+  free(off); free(picked); free(covered); free(list); free(fill); free(rank); free(tid); free(tgain); free(tavail);
   return 0;
 }
 

@@ -468,3 +468,53 @@ def test_solve_quality_against_bruteforce(gseed):
     assert D(ids.tolist()) >= (1 - 1 / math.e - 0.2) * opt - 1e-9
     assert res["hits"] == 2 * res["hits_Rprime"] and res["rounds_t"] >= 1
     assert res["spread_base_est"] == pytest.approx(n * res["hits"] / res["attempts"], rel=1e-15)
+
+
+# ----------------------------------------------------------------------------- harness
+@pytest.mark.parametrize("want,chunk", [(3000, 4096), (2500, 1000), (1, 700)])
+def test_threaded_stream_equals_sequential(want, chunk):
+    """The threaded stream harness (consecutive attempt ranges joined in order) yields
+    exactly the sequential stream: same walks, same attempt count, same next attempt."""
+    d = synth.workload_c1()
+    g = oracle.Graph(d["n"], d["src"], d["dst"], d["w"])
+    q = oracle.Query(g, d["sources"], seed=4)
+    a = oracle.Stream(q, first_aid=777).extend(want)
+    b = oracle.Stream(q, first_aid=777).extend_threads(want, threads=3, chunk=chunk)
+    A, B = a.export(), b.export()
+    assert len(A) == len(B) == want
+    for x, y in ((A.aid, B.aid), (A.node_off, B.node_off), (A.nodes, B.nodes), (A.edges, B.edges)):
+        assert np.array_equal(x, y)
+    assert a.attempts == b.attempts and a._next == b._next == int(A.aid[-1]) + 1
+    # both continue identically
+    a.extend(want + 500)
+    b.extend_threads(want + 500, threads=2, chunk=chunk)
+    assert np.array_equal(a.export().aid, b.export().aid) and a.attempts == b.attempts
+
+
+def test_greedy_kept_gains_equals_recount():
+    """The greedy that keeps and decrements gains returns exactly the picks and gains of the
+    greedy that recounts them every round (Alg. 4 / 7, same tie and zero-gain rules), on
+    the C1 stream and an R-MAT 14 stream, both modes, with candidate masks and with k
+    large enough to reach zero-gain picks."""
+    cases = []
+    d = synth.workload_c1()
+    g = oracle.Graph(d["n"], d["src"], d["dst"], d["w"])
+    cases.append((g, oracle.Stream(oracle.Query(g, d["sources"], seed=4)).extend(4000)))
+    r = synth.workload_rmat(14, "random", 50, 20, "node")
+    gr = oracle.Graph(r["n"], r["src"], r["dst"], r["w"])
+    cases.append((gr, oracle.Stream(oracle.Query(gr, r["sources"], seed=4)).extend(3000)))
+    for g, st in cases:
+        W = st.export()
+        for mode in (oracle.MODE_EDGE, oracle.MODE_NODE):
+            M = g.m if mode == oracle.MODE_EDGE else g.n
+            touched = np.unique(W.elements(mode)[0]).size
+            for k, first, count in ((1, 0, len(W)), (50, 100, len(W) - 300), (min(M, touched + 20), 0, len(W))):
+                a = st.greedy(mode, first, count, M, k)
+                b = st.greedy(mode, first, count, M, k, kept_gains=True)
+                assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+            cm = (np.arange(M) % 3 != 1).astype(np.uint8)
+            a = st.greedy(mode, 0, len(W), M, 40, cand_mask=cm)
+            b = st.greedy(mode, 0, len(W), M, 40, cand_mask=cm, kept_gains=True)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    with pytest.raises(ValueError):
+        cases[0][1].greedy(oracle.MODE_NODE, 0, 10, 3, 4, kept_gains=True)  # k > |C|
