@@ -132,8 +132,17 @@ def query_for(hs, d, seed):
     return hs.Query(sources=d["sources"], mode=mode, k=d["k"], sampling=hs.HSAW_STOP_RULE, eps=d["eps"], seed=seed)
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(d, seed, seconds):
-    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+    """The oracle as it stands on a bounded sample of the same workload: on every host core
+    (consecutive attempt ranges, one per thread, joined in attempt order) and on one core
+    (the paper's single-core convention)."""
     import oracle
     t0 = time.time()
     og = oracle.Graph(d["n"], d["src"], d["dst"], d["w"])
@@ -143,41 +152,55 @@ def cpu_baseline(d, seed, seconds):
     t0 = time.time()
     cal.extend(1 << 62, max_attempts=20_000)
     rate = 20_000 / max(time.time() - t0, 1e-6)
-    attempts = max(20_000, int(rate * seconds))
+    attempts = max(20_000, int(rate * seconds / 2))
     st = oracle.Stream(q)
     t0 = time.time()
     st.extend(1 << 62, max_attempts=attempts)
+    dt1 = time.time() - t0
+    one = {"value": len(st) / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"first {attempts} attempts of the query stream ({len(st)} HSAWs, {dt1:.1f} s)"}
+    cores = host_cores()
+    chunk = max(1024, attempts // 4)
+    attempts_all = chunk * cores * 4
+    st = oracle.Stream(q)
+    t0 = time.time()
+    st.extend_threads(1 << 62, threads=cores, max_attempts=attempts_all, chunk=chunk)
     dt = time.time() - t0
-    return {"value": len(st) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {attempts} attempts of the same query stream ({len(st)} HSAWs, {dt:.1f} s, "
-                      f"oracle graph build {build_s:.0f} s untimed)"}
+    return {"value": len(st) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {attempts_all} attempts of the same query stream on {cores} threads "
+                      f"({len(st)} HSAWs, {dt:.1f} s; oracle graph build {build_s:.0f} s untimed)",
+            "single_core": one}
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle timed on bounded samples of the same workload."""
+    """--impl reference: the CPU oracle, as it stands, timed on every host core over bounded
+    samples of the same workload (each step: the next attempts of the query stream)."""
     if rank != 0:
         return
     import oracle
     d = make_workload(args.scale, args.workload)
     og = oracle.Graph(d["n"], d["src"], d["dst"], d["w"])
     q = oracle.Query(og, d["sources"], seed=synth.SEED_WALKS)
-    per_step = args.ref_attempts
+    cores = host_cores()
+    chunk = max(1024, args.ref_attempts // 4)
+    per_step = chunk * cores * 4
     st = oracle.Stream(q)
     for _ in range(args.warmup):
-        st.extend(1 << 62, max_attempts=max(1000, per_step // 10))
+        st.extend_threads(1 << 62, threads=cores, max_attempts=chunk * cores, chunk=chunk)
     hits0 = len(st)
     t0 = time.time()
     for _ in range(args.steps):
-        st.extend(1 << 62, max_attempts=per_step)
+        st.extend_threads(1 << 62, threads=cores, max_attempts=per_step, chunk=chunk)
     dt = time.time() - t0
     v = (len(st) - hits0) / dt
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"impl": "reference", "metric": METRIC_OTHER.get(args.workload, METRIC), "value": v, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"],
                        "eps": d.get("eps"), "n_hsaw": d.get("n_hsaw"), "delta": "1/n", "parallelism": f"replicas{world}"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} attempts per step of the query stream"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} attempts per step of the query stream on {cores} threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -217,7 +240,7 @@ def batch_workload(count, n_max, n_hsaw, seed=1):
     return inst
 
 
-def run_batch_mode(args, hs, torch):
+def run_batch_mode(args, hs, torch, emit=True):
     t0 = time.time()
     inst = batch_workload(args.batch_count, args.batch_nmax, args.batch_nhsaw)
     gen_s = time.time() - t0
@@ -260,7 +283,9 @@ def run_batch_mode(args, hs, torch):
                        "edges_total": int(sum(x["m"] for x in inst))},
             "serial_solves_per_s": n / t_serial, "batched_vs_serial": t_serial / t_batch,
             "identical_to_serial": bool(identical), "gpu_launches": prof["kernel_launches"], "clocks": ck}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def serve_queries(count, graphs_meta, min_sources, seed=5):
@@ -290,7 +315,7 @@ def serve_pool_sizes(pool_attempts, ns):
     return [max(1 << 22, (pool_attempts * n // n_max) >> 22 << 22) for n in ns]
 
 
-def run_serve_mode(args, hs, torch):
+def run_serve_mode(args, hs, torch, emit=True):
     scales = [int(x) for x in args.serve_scales.split(",")]
     gm, graphs = [], []
     for sc in scales:
@@ -374,7 +399,9 @@ def run_serve_mode(args, hs, torch):
             "serial_solves_per_s": serial_rate, "served_vs_serial": best["solves_per_s"] / serial_rate,
             "serial_pooled_solves_per_s": serial_pooled, "serial_pooled_device_ms_by_phase": serial_pooled_phase,
             "per_rate": per_rate, "identical_to_alone": bool(identical), "clocks": ck}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_sweep_mode(args, hs, torch):
@@ -416,6 +443,26 @@ def run_sweep_mode(args, hs, torch):
     print(json.dumps(line), flush=True)
 
 
+def run_probe_mode(args, hs, torch):
+    """Dependent random 32-byte reads per second (the walk's memory pattern without its
+    arithmetic) over tables from L2-resident to the size of the billion-edge walk records,
+    with 1, 2 and 4 independent chains per lane: the random-request ceiling the sampler's
+    draws/s is compared with."""
+    rows = []
+    for gb in [float(x) for x in args.probe_gb.split(",")]:
+        for chains in (1, 2, 4):
+            rate, ms = hs.hsaw_probe_gather(int(gb * (1 << 30)), chains, max(256, 8192 // chains))
+            rows.append({"table_gb": gb, "chains_per_lane": chains, "reads_per_s": rate, "ms": ms,
+                         "gb_per_s_32B": rate * 32 / 1e9})
+            print(json.dumps({"probe_point": rows[-1]}), file=sys.stderr, flush=True)
+    big = [r for r in rows if r["table_gb"] == max(x["table_gb"] for x in rows)]
+    line = {"metric": "dependent random 32-byte reads/s (gather ceiling probe)",
+            "value": max(r["reads_per_s"] for r in big), "unit": "reads/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": "gather-probe", "tables_gb": args.probe_gb}, "points": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,9 +473,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-attempts", type=int, default=50_000)
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "sweep"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served workloads")
+    ap.add_argument("--ref-attempts", type=int, default=40_000)
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "sweep", "probe"])
     ap.add_argument("--sweep-scales", default="13,17,20,23,27")
+    ap.add_argument("--probe-gb", default="0.0625,1,8,32")
     ap.add_argument("--sweep-density", default="5,10,15")
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
     ap.add_argument("--batch-count", type=int, default=256)
@@ -440,7 +489,7 @@ def main():
     ap.add_argument("--serve-rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--serve-min-sources", type=int, default=16)
-    ap.add_argument("--serve-pool-attempts", type=float, default=0)
+    ap.add_argument("--serve-pool-attempts", type=float, default=536870912)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -459,6 +508,8 @@ def main():
         return run_serve_mode(args, hs, torch)
     if args.mode == "sweep":
         return run_sweep_mode(args, hs, torch)
+    if args.mode == "probe":
+        return run_probe_mode(args, hs, torch)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -549,19 +600,29 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(d, seed, args.cpu_seconds)
     gbytes = 16.0 * d["n"] + 56.0 * d["m"]  # node records + edge, walk-record and index arrays
+    config = {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"],
+              "eps": d.get("eps"), "n_hsaw": d.get("n_hsaw"), "delta": "1/n", "parallelism": f"replicas{world}",
+              "l2": (f"inputs larger than L2 ({gbytes / 1e9:.2f} GB graph)" if gbytes > 129e6 else
+                     f"inputs fit L2 ({gbytes / 1e6:.0f} MB graph, not flushed: diagnostic only)"),
+              "hits_per_step": hits / args.steps,
+              "rounds_t": rounds[-1], "graph_gen_s": d["gen_s"], "graph_ingest_s": ingest_s}
     line = {
-        "metric": METRIC_OTHER.get(args.workload, METRIC), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC_OTHER.get(args.workload, METRIC), "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32", "data": "synthetic",
-        "config": {"workload": d["name"], "n": d["n"], "m": d["m"], "sources": len(d["sources"]), "k": d["k"],
-                   "eps": d.get("eps"), "n_hsaw": d.get("n_hsaw"), "delta": "1/n", "parallelism": f"replicas{world}",
-                   "l2": (f"inputs larger than L2 ({gbytes / 1e9:.2f} GB graph)" if gbytes > 129e6 else
-                          f"inputs fit L2 ({gbytes / 1e6:.0f} MB graph, not flushed: diagnostic only)"),
-                   "hits_per_step": hits / args.steps,
-                   "rounds_t": rounds[-1], "graph_gen_s": d["gen_s"], "graph_ingest_s": ingest_s},
+        "dtype": "u32", "data": "synthetic", "config": config,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["kernel_launches"],
         "clocks": ck,
     }
+    if world == 1 and not args.no_extras:
+        # the batched and served workloads, on the same GPU once the billion-edge graph is freed
+        g.close()
+        del g, d
+        import gc
+        gc.collect()
+        torch.cuda.synchronize()
+        line["batched"] = run_batch_mode(args, hs, torch, emit=False)
+        line["served"] = run_serve_mode(args, hs, torch, emit=False)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

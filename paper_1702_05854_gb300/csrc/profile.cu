@@ -1,6 +1,7 @@
 // Measurement counters: kernel launches and CUDA-event timing of sampler launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -150,3 +151,97 @@ hsaw_status hsaw_profile_read(hsaw_profile* out) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ random-gather probe
+// The ceiling the sampler's memory pattern runs into: every lane follows a chain of
+// dependent reads of random 32-byte records (the size of a walk record), one record per
+// step, the next index taken from the record just read - the same one-dependent-read-per-
+// draw pattern as a walk, with no Philox or walk logic around it.  `chains` independent
+// chains per lane show whether more requests in flight would raise the rate.
+namespace hsaw {
+
+__device__ __forceinline__ uint32_t probe_mix(uint32_t x) {  // 32-bit integer finaliser (Murmur3 fmix32)
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return x;
+}
+
+__global__ void k_probe_fill(uint4* __restrict__ t, uint64_t n_records, uint32_t salt) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_records;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t h = probe_mix((uint32_t)i ^ probe_mix((uint32_t)(i >> 32) + salt));
+    t[2 * i] = make_uint4(h, h ^ 0x9E3779B9u, (uint32_t)i, 0u);
+    t[2 * i + 1] = make_uint4(~h, 0u, 0u, 0u);
+  }
+}
+
+template <int CHAINS>
+__global__ void __launch_bounds__(256, 6) k_probe_gather(const uint4* __restrict__ t, uint64_t n_records,
+                                                         uint32_t steps, unsigned long long* __restrict__ sink) {
+  const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t idx[CHAINS];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) idx[c] = (uint32_t)(((uint64_t)probe_mix(gid * CHAINS + c + 1) * n_records) >> 32);
+  for (uint32_t s = 0; s < steps; ++s) {
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) {
+      const uint4 a = __ldg(&t[2 * (size_t)idx[c]]);
+      const uint4 b = __ldg(&t[2 * (size_t)idx[c] + 1]);
+      acc += a.w + b.y;
+      idx[c] = (uint32_t)(((uint64_t)probe_mix(a.x ^ (s * 0x27D4EB2Fu) ^ gid) * n_records) >> 32);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) acc += idx[c];
+  if (acc == 0x12345678u) atomicAdd(sink, 1ull);  // keeps the loads live; practically never taken
+}
+
+}  // namespace hsaw
+
+extern "C" hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, uint32_t steps, double* reads_per_s,
+                                         double* ms, void* stream) {
+  using namespace hsaw;
+  if (!reads_per_s || table_bytes < 64 || (chains != 1 && chains != 2 && chains != 4) || steps < 1)
+    return fail(HSAW_E_INVALID, "probe: need table_bytes >= 64, chains in {1, 2, 4}, steps >= 1");
+  const uint64_t n_records = std::min<uint64_t>(table_bytes / 32, 1ull << 32);
+  cudaStream_t s = (cudaStream_t)stream;
+  void* t = nullptr;
+  HSAW_TRY(dmalloc(&t, n_records * 32 + 64, s));
+  unsigned long long* sink = reinterpret_cast<unsigned long long*>((char*)t + n_records * 32);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  hsaw_status st = HSAW_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(HSAW_E_DEVICE, "probe: events");
+  int bps = 0;
+  if (st == HSAW_OK) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_probe_gather<1>, 256, 0);
+    count_launch();
+    k_probe_fill<<<sm_count() * 8, 256, 0, s>>>((uint4*)t, n_records, 0x5EEDu);
+    cudaMemsetAsync(sink, 0, 8, s);
+    const unsigned grid = (unsigned)(sm_count() * std::max(bps, 1));
+    for (int rep = 0; rep < 2 && st == HSAW_OK; ++rep) {  // the first pass warms up, the second is timed
+      cudaEventRecord(e0, s);
+      count_launch();
+      if (chains == 1) k_probe_gather<1><<<grid, 256, 0, s>>>((const uint4*)t, n_records, steps, sink);
+      else if (chains == 2) k_probe_gather<2><<<grid, 256, 0, s>>>((const uint4*)t, n_records, steps, sink);
+      else k_probe_gather<4><<<grid, 256, 0, s>>>((const uint4*)t, n_records, steps, sink);
+      cudaEventRecord(e1, s);
+      if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        st = fail(HSAW_E_DEVICE, "probe: launch failed");
+    }
+    float t_ms = 0.f;
+    if (st == HSAW_OK) {
+      cudaEventElapsedTime(&t_ms, e0, e1);
+      *reads_per_s = (double)grid * 256.0 * chains * steps / (t_ms * 1e-3);
+      if (ms) *ms = t_ms;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(t, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
