@@ -39,18 +39,23 @@ BYTES_PER_STEP = 96  # three random 32-byte sectors per live-edge draw: node rec
 # DRAM bytes (read + write) per live-edge draw of the sampler kernel from an ncu capture,
 # keyed by (hash of the kernel's source, workload).  A workload without a capture of the
 # current kernel reports traffic = null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("62b084bf844e", "rmat22-wc-eSI"): 122.9,   # profiles/k_sample_rmat22_dram.md
+               ("62b084bf844e", "rmat26-wc-eSI"): 122.9}   # the scale-22 figure, scaled by draws
 
 
 def sampler_hash():
-    """Hash of k_sample's own source text and the device helpers it calls (common.cuh)."""
+    """Hash of k_sample's own source text and the device helpers it calls (Philox, draws,
+    edge pick, checkpoints in common.cuh)."""
     csrc = os.path.join(ROOT, "paper_1702_05854_gb300", "csrc")
     src = open(os.path.join(csrc, "sample.cu")).read()
     i = src.index("template <bool HAS_P, bool HAS_REM>\n__global__ void __launch_bounds__(256, 6) k_sample")
     j = src.index("\n}\n", i)
+    common = open(os.path.join(csrc, "common.cuh")).read()
+    a = common.index("// ------------------------------------------------------------------ Philox4x32-10")
+    b = common.index("// ------------------------------------------------------------------ primitives")
     h = hashlib.sha1()
     h.update(src[i:j].encode())
-    h.update(open(os.path.join(csrc, "common.cuh"), "rb").read())
+    h.update(common[a:b].encode())
     return h.hexdigest()[:12]
 
 
@@ -450,10 +455,11 @@ def run_probe_mode(args, hs, torch):
     draws/s is compared with."""
     rows = []
     for gb in [float(x) for x in args.probe_gb.split(",")]:
-        for chains in (1, 2, 4):
-            rate, ms = hs.hsaw_probe_gather(int(gb * (1 << 30)), chains, max(256, 8192 // chains))
-            rows.append({"table_gb": gb, "chains_per_lane": chains, "reads_per_s": rate, "ms": ms,
-                         "gb_per_s_32B": rate * 32 / 1e9})
+        for chains, bps in [(1, b) for b in (1, 2, 3, 4, 5, 6)] + [(2, 6), (2, 3), (4, 6)]:
+            steps = max(256, 8192 * bps // (6 * chains))
+            rate, ms = hs.hsaw_probe_gather(int(gb * (1 << 30)), chains, steps, bps)
+            rows.append({"table_gb": gb, "chains_per_lane": chains, "blocks_per_sm": bps, "reads_per_s": rate,
+                         "ms": ms, "gb_per_s_32B": rate * 32 / 1e9})
             print(json.dumps({"probe_point": rows[-1]}), file=sys.stderr, flush=True)
     big = [r for r in rows if r["table_gb"] == max(x["table_gb"] for x in rows)]
     line = {"metric": "dependent random 32-byte reads/s (gather ceiling probe)",
@@ -477,7 +483,7 @@ def main():
     ap.add_argument("--ref-attempts", type=int, default=40_000)
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "sweep", "probe"])
     ap.add_argument("--sweep-scales", default="13,17,20,23,27")
-    ap.add_argument("--probe-gb", default="0.0625,1,8,32")
+    ap.add_argument("--probe-gb", default="0.0625,0.25,1,8,32")
     ap.add_argument("--sweep-density", default="5,10,15")
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
     ap.add_argument("--batch-count", type=int, default=256)

@@ -309,13 +309,14 @@ HSAW_API hsaw_status hsaw_profile_read(hsaw_profile* out);
 /* Random-gather probe (measurement, not part of the method): the rate of dependent random
  * 32-byte reads the GPU sustains, the memory pattern of a walk (one dependent record read
  * per live-edge draw) without the walk's arithmetic.  Allocates a table of table_bytes
- * (rounded down to 32-byte records, at most 2^32 of them), fills it, and runs one lane per
- * thread on every SM, each following `chains` independent chains (1, 2 or 4) of `steps`
+ * (rounded down to 32-byte records, at most 2^32 of them), fills it, and runs blocks of
+ * 256 threads, blocks_per_sm of them per SM (<= 0 or above what fits: as many as fit,
+ * at most 6), each thread following `chains` independent chains (1, 2 or 4) of `steps`
  * dependent reads; the second of two passes is timed with CUDA events on `stream`.
  * *reads_per_s = records read / time, *ms (may be NULL) = the timed pass.  Errors:
  * HSAW_E_INVALID, HSAW_E_NOMEM, HSAW_E_DEVICE. */
-HSAW_API hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, uint32_t steps, double* reads_per_s,
-                                       double* ms, void* stream);
+HSAW_API hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, uint32_t steps, int32_t blocks_per_sm,
+                                       double* reads_per_s, double* ms, void* stream);
 
 /* ------------------------------------------------------------------ diagnostics */
 HSAW_API const char* hsaw_last_error(void); /* thread-local message of the last failing call */

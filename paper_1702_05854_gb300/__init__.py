@@ -85,7 +85,8 @@ SIGNATURES = {
     "hsaw_server_destroy": (ctypes.c_int, [_p]),
     "hsaw_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "hsaw_profile_read": (ctypes.c_int, [ctypes.POINTER(hsaw_profile)]),
-    "hsaw_probe_gather": (ctypes.c_int, [_u64, _i32, ctypes.c_uint32, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), _p]),
+    "hsaw_probe_gather": (ctypes.c_int, [_u64, _i32, ctypes.c_uint32, _i32, ctypes.POINTER(_dbl),
+                                         ctypes.POINTER(_dbl), _p]),
     "hsaw_last_error": (ctypes.c_char_p, []),
     "hsaw_version": (ctypes.c_char_p, []),
 }
@@ -479,10 +480,11 @@ def hsaw_profile_read():
     return d
 
 
-def hsaw_probe_gather(table_bytes: int, chains: int = 1, steps: int = 256, stream=None):
+def hsaw_probe_gather(table_bytes: int, chains: int = 1, steps: int = 256, blocks_per_sm: int = 0, stream=None):
     """(dependent random 32-byte reads per second, timed ms) over a table of table_bytes."""
     r, ms = _dbl(), _dbl()
-    _check(load().hsaw_probe_gather(table_bytes, chains, steps, ctypes.byref(r), ctypes.byref(ms), _stream(stream)))
+    _check(load().hsaw_probe_gather(table_bytes, chains, steps, blocks_per_sm, ctypes.byref(r), ctypes.byref(ms),
+                                    _stream(stream)))
     return r.value, ms.value
 
 

@@ -487,6 +487,7 @@ hsaw_status hsaw_graph_from_csr(int64_t n, int64_t m, const int64_t* in_row_ptr,
 hsaw_status hsaw_graph_destroy(hsaw_graph g) {
   if (!g) return HSAW_OK;
   cudaDeviceSynchronize();
+  sample_tune_forget(g->g);
   destroy_graph(g->g);
   delete g;
   return HSAW_OK;

@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(256, 6) k_probe_gather(const uint4* __restrict
 
 }  // namespace hsaw
 
-extern "C" hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, uint32_t steps, double* reads_per_s,
-                                         double* ms, void* stream) {
+extern "C" hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, uint32_t steps, int32_t blocks_per_sm,
+                                         double* reads_per_s, double* ms, void* stream) {
   using namespace hsaw;
   if (!reads_per_s || table_bytes < 64 || (chains != 1 && chains != 2 && chains != 4) || steps < 1)
     return fail(HSAW_E_INVALID, "probe: need table_bytes >= 64, chains in {1, 2, 4}, steps >= 1");
@@ -221,6 +221,7 @@ extern "C" hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, u
     count_launch();
     k_probe_fill<<<sm_count() * 8, 256, 0, s>>>((uint4*)t, n_records, 0x5EEDu);
     cudaMemsetAsync(sink, 0, 8, s);
+    if (blocks_per_sm > 0) bps = std::min(bps, (int)blocks_per_sm);
     const unsigned grid = (unsigned)(sm_count() * std::max(bps, 1));
     for (int rep = 0; rep < 2 && st == HSAW_OK; ++rep) {  // the first pass warms up, the second is timed
       cudaEventRecord(e0, s);

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "solver.cuh"
@@ -353,6 +354,66 @@ static int sample_blocks_per_sm() {
   return cached;
 }
 
+// Sampler occupancy autotuner.  A walk makes one dependent record read per draw; with the
+// records in DRAM the random-read rate of this GPU peaks at 1-2 blocks of 256 per SM and
+// falls a little as more requests queue, while graphs whose records sit in L2 are bound by
+// issue and want every warp.  So each graph's first four sampler launches of at least 2^22
+// attempts run with 6, 4, 3 and 2 blocks per SM (draws per ms by CUDA events on the
+// launching stream), and its later launches use the fastest (6 unless another is faster by
+// more than 3%).  The grid does not change any result: hits are ordered by attempt id.
+// HSAW_SAMPLE_BLOCKS=b in the environment forces b blocks per SM (measurement).
+namespace {
+constexpr int kTuneCands[4] = {6, 4, 3, 2};
+struct SampleTune {
+  int next_trial = 0, done = 0, best = 0;
+  float rate[4] = {0.f, 0.f, 0.f, 0.f};
+};
+std::mutex g_stune_mu;
+std::unordered_map<const void*, SampleTune> g_stune;  // keyed by the graph's node array
+}  // namespace
+
+void sample_tune_forget(const Graph& g) {
+  std::lock_guard<std::mutex> lk(g_stune_mu);
+  g_stune.erase(g.node);
+}
+
+int sample_tuned_blocks(const Graph& g) {
+  std::lock_guard<std::mutex> lk(g_stune_mu);
+  auto it = g_stune.find(g.node);
+  return it == g_stune.end() ? 0 : it->second.best;
+}
+
+// Blocks per SM for the next launch over `batch` attempts; *trial >= 0 when it is a timed trial.
+static int sample_blocks_for(const Graph& g, uint64_t batch, int* trial) {
+  *trial = -1;
+  const int full = sample_blocks_per_sm();
+  if (const char* f = getenv("HSAW_SAMPLE_BLOCKS")) {
+    const int b = atoi(f);
+    return std::max(1, std::min(full, b > 0 ? b : full));
+  }
+  std::lock_guard<std::mutex> lk(g_stune_mu);
+  SampleTune& t = g_stune[g.node];
+  if (t.best) return std::min(full, t.best);
+  if (batch < (1ull << 22) || t.next_trial >= 4) return full;
+  *trial = t.next_trial++;
+  return std::min(full, kTuneCands[*trial]);
+}
+
+static void sample_tune_record(const Graph& g, int trial, double draws, float ms) {
+  if (trial < 0 || !(ms > 0.f)) return;
+  std::lock_guard<std::mutex> lk(g_stune_mu);
+  SampleTune& t = g_stune[g.node];
+  t.rate[trial] = (float)(draws / ms);
+  if (++t.done < 4) return;
+  int best = 0;
+  for (int i = 1; i < 4; ++i)
+    if (t.rate[i] > t.rate[best] * 1.03f) best = i;
+  t.best = kTuneCands[best];
+  if (getenv("HSAW_LOG_LAUNCHES"))
+    fprintf(stderr, "hsaw: k_sample tuned blocks_per_sm=%d (G draws/s: 6 %.1f, 4 %.1f, 3 %.1f, 2 %.1f)\n", t.best,
+            t.rate[0] / 1e6, t.rate[1] / 1e6, t.rate[2] / 1e6, t.rate[3] / 1e6);
+}
+
 static void launch_sample(const SampleParams& P, unsigned grid, cudaStream_t s) {
   const bool hp = P.p32 != nullptr, hr = (P.edge_removed || P.node_removed);
   if (hp && hr) { count_launch(); k_sample<true, true><<<grid, 256, 0, s>>>(P); }
@@ -390,13 +451,19 @@ static hsaw_status sample_window(const Graph& g, const QueryDev& qd, Stream& st,
     P.chunk_hits = st.chunk_hits.p;
     P.recs = st.recs.p;
     P.steps = d_steps;
-    const unsigned grid = (unsigned)std::max(1, std::min<int>(sm_count() * sample_blocks_per_sm(),
-                                                               (int)((n_chunks + 7) / 8)));
+    int trial = -1;
+    const int bps = sample_blocks_for(g, batch, &trial);
+    const unsigned grid = (unsigned)std::max(1, std::min<int>(sm_count() * bps, (int)((n_chunks + 7) / 8)));
+    cudaEvent_t tev[2] = {nullptr, nullptr};
+    if (trial >= 0 && (cudaEventCreate(&tev[0]) != cudaSuccess || cudaEventCreate(&tev[1]) != cudaSuccess)) {
+      cudaGetLastError();
+      trial = -1;
+    }
+    if (trial >= 0) cudaEventRecord(tev[0], s);
     void* prof = profile_begin(s);
     launch_sample(P, grid, s);
     profile_end(prof, s, batch);
-    if (getenv("HSAW_LOG_LAUNCHES"))  // measurement aid: attempts of each sampler launch
-      fprintf(stderr, "hsaw: k_sample launch attempts=%llu\n", (unsigned long long)batch);
+    if (trial >= 0) cudaEventRecord(tev[1], s);
     HSAW_CK(cudaGetLastError());
     count_launch();
     k_clamp<<<grid_for(n_chunks, 256, 4096), 256, 0, s>>>(st.chunk_hits.p, st.chunk_off.p, n_chunks, cap);
@@ -407,6 +474,12 @@ static hsaw_status sample_window(const Graph& g, const QueryDev& qd, Stream& st,
     HSAW_CK(cudaMemcpyAsync(h, st.ctrs.p, 16, cudaMemcpyDeviceToHost, s));
     HSAW_CK(cudaMemcpyAsync(&hs, d_steps, 8, cudaMemcpyDeviceToHost, s));
     HSAW_CK(cudaStreamSynchronize(s));
+    if (trial >= 0) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, tev[0], tev[1]) == cudaSuccess) sample_tune_record(g, trial, (double)hs, ms);
+      cudaEventDestroy(tev[0]);
+      cudaEventDestroy(tev[1]);
+    }
     if (h[1] & ST_STEP_CAP) return fail(HSAW_E_STEP_CAP, "sampling: a walk exceeded its step guard");
     if ((h[1] & ST_OVERFLOW) && cap < CHUNK) {
       cap = CHUNK;  // rare: rerun this launch with room for every attempt to hit
@@ -414,6 +487,9 @@ static hsaw_status sample_window(const Graph& g, const QueryDev& qd, Stream& st,
     }
     st.steps += hs;
     profile_add_steps(hs);
+    if (getenv("HSAW_LOG_LAUNCHES"))  // measurement aid: attempts and live-edge draws of each sampler launch
+      fprintf(stderr, "hsaw: k_sample launch attempts=%llu draws=%llu blocks_per_sm=%d\n", (unsigned long long)batch,
+              hs, bps);
     *new_hits = h[2];
     if (h[2]) {
       HSAW_TRY(st.aid.ensure((size_t)st.count + h[2], s, true));
