@@ -357,16 +357,18 @@ static int sample_blocks_per_sm() {
 // Sampler occupancy autotuner.  A walk makes one dependent record read per draw; with the
 // records in DRAM the random-read rate of this GPU peaks at 1-2 blocks of 256 per SM and
 // falls a little as more requests queue, while graphs whose records sit in L2 are bound by
-// issue and want every warp.  So each graph's first four sampler launches of at least 2^22
-// attempts run with 6, 4, 3 and 2 blocks per SM (draws per ms by CUDA events on the
-// launching stream), and its later launches use the fastest (6 unless another is faster by
-// more than 3%).  The grid does not change any result: hits are ordered by attempt id.
-// HSAW_SAMPLE_BLOCKS=b in the environment forces b blocks per SM (measurement).
+// issue and want every warp.  So each graph's first two sampler launches of at least 2^23
+// attempts run with 6 and 3 blocks per SM (draws per ms by CUDA events on the launching
+// stream), and its later launches use 3 if it was faster by more than 3%, else 6.  (Trials
+// at 4 and 2 blocks per SM gained nothing on the billion-edge graph and cost up to 47% of a
+// launch on L2-resident ones.)  The grid does not change any result: hits are ordered by
+// attempt id.  HSAW_SAMPLE_BLOCKS=b in the environment forces b blocks per SM (measurement).
 namespace {
-constexpr int kTuneCands[4] = {6, 4, 3, 2};
+constexpr int kTuneN = 2;
+constexpr int kTuneCands[kTuneN] = {6, 3};
 struct SampleTune {
   int next_trial = 0, done = 0, best = 0;
-  float rate[4] = {0.f, 0.f, 0.f, 0.f};
+  float rate[kTuneN] = {0.f, 0.f};
 };
 std::mutex g_stune_mu;
 std::unordered_map<const void*, SampleTune> g_stune;  // keyed by the graph's node array
@@ -394,7 +396,7 @@ static int sample_blocks_for(const Graph& g, uint64_t batch, int* trial) {
   std::lock_guard<std::mutex> lk(g_stune_mu);
   SampleTune& t = g_stune[g.node];
   if (t.best) return std::min(full, t.best);
-  if (batch < (1ull << 22) || t.next_trial >= 4) return full;
+  if (batch < (1ull << 23) || t.next_trial >= kTuneN) return full;
   *trial = t.next_trial++;
   return std::min(full, kTuneCands[*trial]);
 }
@@ -404,14 +406,14 @@ static void sample_tune_record(const Graph& g, int trial, double draws, float ms
   std::lock_guard<std::mutex> lk(g_stune_mu);
   SampleTune& t = g_stune[g.node];
   t.rate[trial] = (float)(draws / ms);
-  if (++t.done < 4) return;
+  if (++t.done < kTuneN) return;
   int best = 0;
-  for (int i = 1; i < 4; ++i)
+  for (int i = 1; i < kTuneN; ++i)
     if (t.rate[i] > t.rate[best] * 1.03f) best = i;
   t.best = kTuneCands[best];
   if (getenv("HSAW_LOG_LAUNCHES"))
-    fprintf(stderr, "hsaw: k_sample tuned blocks_per_sm=%d (G draws/s: 6 %.1f, 4 %.1f, 3 %.1f, 2 %.1f)\n", t.best,
-            t.rate[0] / 1e6, t.rate[1] / 1e6, t.rate[2] / 1e6, t.rate[3] / 1e6);
+    fprintf(stderr, "hsaw: k_sample tuned blocks_per_sm=%d (G draws/s: 6 %.1f, 3 %.1f)\n", t.best, t.rate[0] / 1e6,
+            t.rate[1] / 1e6);
 }
 
 static void launch_sample(const SampleParams& P, unsigned grid, cudaStream_t s) {
