@@ -26,6 +26,7 @@ void Cover::release(cudaStream_t s) {
   keys.release(s); vals.release(s); keys2.release(s); vals2.release(s); run_flag.release(s);
   uid.release(s); cnt.release(s); inv_off.release(s); inv_walk.release(s); entry_uidx.release(s);
   walk_eoff.release(s); cnt_work.release(s); covered.release(s); dirty.release(s); partial.release(s);
+  inv_ent.release(s);
 }
 
 // entry offsets of walks [first, first + count) relative to the first walk's first entry
@@ -435,11 +436,15 @@ __global__ void __launch_bounds__(512) k_greedy(GreedyParams P) {
 }
 
 // ------------------------------------------------------------------ greedy on one cluster
-// The same greedy on one thread-block cluster: the per-group largest counts live in the
-// CTAs' shared memory (CTA r owns groups [r * per_cta, (r + 1) * per_cta)), decrements
-// mark the owner's dirty bit with an atomic on its shared memory (distributed shared
-// memory), and phases are separated by the hardware cluster barrier instead of a barrier
-// on global memory.  Group g covers elements [g << gshift, (g + 1) << gshift).
+// The same greedy on one thread-block cluster.  The per-group largest keys live in the
+// CTAs' shared memory (CTA r owns groups [r * per_cta, (r + 1) * per_cta)); group g covers
+// elements [g << gshift, (g + 1) << gshift).  Counts only fall, so a group's largest key
+// changes only when the count of that key's own element changes: a thread that decrements
+// element x reads the largest key of x's group from its owner (distributed shared memory)
+// and, only if x is that key's element, marks the group stale there.  The next pick
+// rescans just the stale groups.  Each entry of the inverted index carries its walk's
+// entry range, so covering a walk needs no separate offset lookup, and the walk's first
+// element id is fetched together with its covered flag.
 namespace cg = cooperative_groups;
 
 constexpr unsigned long long KEY_UNKNOWN = ~0ull;  // above every element key (counts < 2^31)
@@ -450,14 +455,26 @@ struct ClusterGreedyParams {
   int32_t k;
   uint32_t* cnt;  // running counts | EXCLUDED
   const uint32_t* inv_off;
-  const uint32_t* inv_walk;
-  const uint32_t* walk_eoff;
+  const uint4* inv_ent;  // {walk, first entry, end entry, 0} per inverted-index entry
   const uint32_t* entry_uidx;
   uint8_t* covered;
   uint32_t* out_u;
   uint32_t* out_gain;
   uint32_t* ctl;  // [3] rounds done
 };
+
+// One decrement of element x: its running count, and the stale bit of its group in the
+// owner CTA when x is the element of that group's largest key.
+__device__ __forceinline__ void cover_decrement(const ClusterGreedyParams& P, cg::cluster_group& cluster,
+                                                unsigned long long* gkey, uint32_t* sbits, uint32_t x) {
+  atomicSub(&P.cnt[x], 1u);
+  const uint32_t gg = x >> P.gshift, owner = gg / P.per_cta, gl = gg % P.per_cta;
+  const unsigned long long top = *cluster.map_shared_rank(&gkey[gl], owner);
+  if (top != 0 && 0xFFFFFFFFu - (uint32_t)top == x) {
+    uint32_t* rb = cluster.map_shared_rank(sbits, owner);
+    atomicOr(&rb[gl >> 5], 1u << (gl & 31));
+  }
+}
 
 __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams P) {
   extern __shared__ unsigned long long gkey[];  // per: largest key of each owned group
@@ -468,40 +485,28 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
   const uint32_t C = cluster.num_blocks();
   const uint32_t per = P.per_cta;
   const uint32_t words = (per + 31) / 32;
-  uint32_t* dbits = reinterpret_cast<uint32_t*>(gkey + per);  // dirty bits of the owned groups
+  uint32_t* sbits = reinterpret_cast<uint32_t*>(gkey + per);  // stale bits of the owned groups
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t gbase = rank * per;
   const uint32_t gend = min(P.NG, gbase + per);
   const uint32_t nown = gend > gbase ? gend - gbase : 0;
-  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dbits[i] = 0xFFFFFFFFu;
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sbits[i] = 0xFFFFFFFFu;
   for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) gkey[i] = KEY_UNKNOWN;
   cluster.sync();
   const uint32_t gsz = 1u << P.gshift;
   int32_t r = 0;
   for (; r < P.k; ++r) {
-    // 1. refresh the owned groups whose counts changed.  Counts only go down, so a group
-    //    keeps its largest key unless the count of that key's own element changed: one lane
-    //    per dirty group re-reads that one count, and only the groups whose largest element
-    //    changed are rescanned, one warp per group.
+    // 1. rescan the owned groups marked stale, one warp per group
     for (uint32_t wi = w; wi < words; wi += nw) {
-      const uint32_t bits = dbits[wi];
+      uint32_t todo = sbits[wi];
       __syncwarp();
-      if (!bits) continue;
-      if (lane == 0) dbits[wi] = 0;
-      const uint32_t gl0 = wi * 32 + lane;
-      bool stale = false;
-      if (((bits >> lane) & 1u) && gl0 < nown) {
-        const unsigned long long k0 = gkey[gl0];
-        if (k0 == KEY_UNKNOWN)
-          stale = true;
-        else if (k0 != 0)  // a group whose keys are all zero stays so
-          stale = __ldcg(&P.cnt[0xFFFFFFFFu - (uint32_t)k0]) != (uint32_t)(k0 >> 32);
-      }
-      uint32_t todo = __ballot_sync(0xffffffffu, stale);
+      if (!todo) continue;
+      if (lane == 0) sbits[wi] = 0;
       while (todo) {
         const uint32_t b = __ffs(todo) - 1;
         todo &= todo - 1;
         const uint32_t gl = wi * 32 + b;
+        if (gl >= nown) continue;
         const uint32_t e0 = (gbase + gl) << P.gshift;
         const uint32_t e1 = min(P.U, e0 + gsz);
         unsigned long long best = 0;
@@ -537,50 +542,49 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
       P.out_gain[r] = gain;
       atomicOr(&P.cnt[u], EXCLUDED);
     }
-    if (threadIdx.x == 0) {  // the picked element's group is dirty in its owner
+    if (threadIdx.x == 0) {  // the picked element's group is stale in its owner
       const uint32_t gg = u >> P.gshift;
-      if (gg / per == rank) atomicOr(&dbits[(gg % per) >> 5], 1u << ((gg % per) & 31));
+      if (gg / per == rank) atomicOr(&sbits[(gg % per) >> 5], 1u << ((gg % per) & 31));
     }
-    // 3. cover its walks: decrement every element of each newly covered walk and mark the
-    //    element's group dirty in the CTA that owns it (one thread per walk when walks are
-    //    short, one warp per walk otherwise)
+    // 3. cover its walks (one thread per walk when walks are short, one warp per walk
+    //    otherwise); the group keys read by cover_decrement do not change until step 1
     const uint32_t q0 = P.inv_off[u], q1 = P.inv_off[u + 1];
     if (P.short_walks) {
       for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
-        const uint32_t j = P.inv_walk[q];
-        const uint8_t was = __ldcg(&P.covered[j]);
-        const uint32_t p0 = P.walk_eoff[j], p1 = P.walk_eoff[j + 1];  // in flight with the flag
-        if (was) continue;
-        P.covered[j] = 1;
-        for (uint32_t p = p0; p < p1; ++p) {
-          const uint32_t x = P.entry_uidx[p];
-          atomicSub(&P.cnt[x], 1u);
-          const uint32_t gg = x >> P.gshift, gl = gg % per;
-          uint32_t* rb = cluster.map_shared_rank(dbits, gg / per);
-          atomicOr(&rb[gl >> 5], 1u << (gl & 31));
-        }
+        const uint4 ent = __ldg(&P.inv_ent[q]);
+        const uint32_t x0 = ent.y < ent.z ? __ldg(&P.entry_uidx[ent.y]) : 0u;  // in flight with the flag
+        if (__ldcg(&P.covered[ent.x])) continue;
+        P.covered[ent.x] = 1;
+        if (ent.y < ent.z) cover_decrement(P, cluster, gkey, sbits, x0);
+        for (uint32_t p = ent.y + 1; p < ent.z; ++p) cover_decrement(P, cluster, gkey, sbits, __ldg(&P.entry_uidx[p]));
       }
-    } else
-    for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
-      const uint32_t j = P.inv_walk[q];
-      uint32_t fresh = 0;
-      if (lane == 0) fresh = __ldcg(&P.covered[j]) ? 0u : 1u;
-      const uint32_t p0 = P.walk_eoff[j], p1 = P.walk_eoff[j + 1];  // in flight with the flag
-      fresh = __shfl_sync(0xffffffffu, fresh, 0);
-      if (!fresh) continue;
-      if (lane == 0) P.covered[j] = 1;
-      for (uint32_t p = p0 + lane; p < p1; p += 32) {
-        const uint32_t x = P.entry_uidx[p];
-        atomicSub(&P.cnt[x], 1u);
-        const uint32_t gg = x >> P.gshift, gl = gg % per;
-        uint32_t* rb = cluster.map_shared_rank(dbits, gg / per);
-        atomicOr(&rb[gl >> 5], 1u << (gl & 31));
+    } else {
+      for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
+        const uint4 ent = __ldg(&P.inv_ent[q]);
+        const uint32_t p = ent.y + lane;
+        const uint32_t x = p < ent.z ? __ldg(&P.entry_uidx[p]) : 0u;  // in flight with the flag
+        uint32_t fresh = 0;
+        if (lane == 0) fresh = __ldcg(&P.covered[ent.x]) ? 0u : 1u;
+        fresh = __shfl_sync(0xffffffffu, fresh, 0);
+        if (!fresh) continue;
+        if (lane == 0) P.covered[ent.x] = 1;
+        if (p < ent.z) cover_decrement(P, cluster, gkey, sbits, x);
+        for (uint32_t pp = p + 32; pp < ent.z; pp += 32) cover_decrement(P, cluster, gkey, sbits, __ldg(&P.entry_uidx[pp]));
       }
     }
     cluster.sync();
   }
   cluster.sync();  // no CTA leaves while a peer may still read its shared memory
   if (rank == 0 && threadIdx.x == 0) P.ctl[3] = (uint32_t)r;
+}
+
+// Inverted-index entries with their walk's entry range: {j, walk_eoff[j], walk_eoff[j + 1], 0}.
+__global__ void k_inv_ranges(const uint32_t* __restrict__ inv_walk, const uint32_t* __restrict__ walk_eoff, uint32_t E,
+                             uint4* __restrict__ inv_ent) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E; q += gridDim.x * blockDim.x) {
+    const uint32_t j = inv_walk[q];
+    inv_ent[q] = make_uint4(j, walk_eoff[j], walk_eoff[j + 1], 0u);
+  }
 }
 
 __global__ void k_greedy_init(const int32_t* __restrict__ uid, const uint32_t* __restrict__ cnt, uint32_t U,
@@ -713,12 +717,28 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
     NG = (uint32_t)(((uint64_t)U + (1ull << gshift) - 1) >> gshift);
     per = (NG + csize - 1) / csize;
   }
+  // smaller groups make a stale group's rescan cheaper (2^gshift / 32 reads per lane) while
+  // the per-pick scan of a CTA's group keys grows: shrink them down to 32 elements while a
+  // CTA owns at most 2,048 groups (two keys per thread)
+  while (gshift > 5) {
+    const uint32_t ng2 = (uint32_t)(((uint64_t)U + (1ull << (gshift - 1)) - 1) >> (gshift - 1));
+    const uint32_t per2 = (ng2 + csize - 1) / csize;
+    if (per2 > 2048 || need(per2) > smem_cap) break;
+    --gshift;
+    NG = ng2;
+    per = per2;
+  }
   const size_t smem = need(per);
   HSAW_TRY(cv.cnt_work.ensure(U, s));
   HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
+  HSAW_TRY(cv.inv_ent.ensure((size_t)cv.entries, s));
   HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
   count_launch();
   k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);
+  HSAW_CK(cudaGetLastError());
+  count_launch();
+  k_inv_ranges<<<grid_for((size_t)cv.entries, 256, 8192), 256, 0, s>>>(cv.inv_walk.p, cv.walk_eoff.p,
+                                                                      (uint32_t)cv.entries, cv.inv_ent.p);
   HSAW_CK(cudaGetLastError());
   ClusterGreedyParams P;
   P.U = U;
@@ -729,8 +749,7 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   P.k = k;
   P.cnt = cv.cnt_work.p;
   P.inv_off = cv.inv_off.p;
-  P.inv_walk = cv.inv_walk.p;
-  P.walk_eoff = cv.walk_eoff.p;
+  P.inv_ent = cv.inv_ent.p;
   P.entry_uidx = cv.entry_uidx.p;
   P.covered = cv.covered.p;
   P.out_u = outs;

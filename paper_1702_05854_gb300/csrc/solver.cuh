@@ -65,6 +65,7 @@ struct Cover {
   DBuf<uint32_t> walk_eoff;                 // walks + 1: entry offsets of the walks
   DBuf<uint32_t> cnt_work;                  // greedy's running counts
   DBuf<uint8_t> covered, dirty;  // greedy: walk covered flags, group dirty flags
+  DBuf<uint4> inv_ent;           // cluster greedy: inverted-index entries with their walk's entry range
   DBuf<unsigned long long> partial;
   void release(cudaStream_t s);
 };
