@@ -334,11 +334,21 @@ def run_serve_mode(args, hs, torch, emit=True):
     if pool_attempts:  # every query on a graph shares its walk seed, so traces can be reused
         for _, kw in qs:
             kw["seed"] = synth.SEED_WALKS
+    if args.serve_max_attempts:  # an attempt budget per query: beyond it, HSAW_E_TIMEOUT
+        for _, kw in qs:
+            kw["max_attempts"] = int(args.serve_max_attempts)
     queries = [(gi, hs.Query(**kw)) for gi, kw in qs]
+
+    def solve(gi, q):
+        try:
+            return (0,) + tuple(hs.hsaw_solve(graphs[gi], q))
+        except hs.HsawError as e:
+            return (e.status, None, None, None)
+
     # serial: one query at a time on the same stream of queries
-    hs.hsaw_solve(graphs[queries[0][0]], queries[0][1])
+    solve(*queries[0])
     t0 = time.perf_counter()
-    alone = [hs.hsaw_solve(graphs[gi], q) for gi, q in queries]
+    alone = [solve(gi, q) for gi, q in queries]
     t_serial = time.perf_counter() - t0
     serial_rate = len(queries) / t_serial
     pool_s, pool_gb = 0.0, 0.0
@@ -351,16 +361,16 @@ def run_serve_mode(args, hs, torch, emit=True):
         torch.cuda.synchronize()
         pool_s = time.perf_counter() - t0
         pool_gb = (free0 - torch.cuda.mem_get_info()[0]) / 1e9
-        hs.hsaw_solve(graphs[queries[0][0]], queries[0][1])
+        solve(*queries[0])
         # serial again, now reading the pools: what reuse alone buys (timed without the
         # library's phase timers, whose events cost host time), then where time goes
         t0 = time.perf_counter()
         for gi, q in queries:
-            hs.hsaw_solve(graphs[gi], q)
+            solve(gi, q)
         serial_pooled = len(queries) / (time.perf_counter() - t0)
         hs.hsaw_profile_enable(True)
         for gi, q in queries:
-            hs.hsaw_solve(graphs[gi], q)
+            solve(gi, q)
         serial_pooled_phase = hs.hsaw_profile_read()["phase_ms"]
         hs.hsaw_profile_enable(False)
     rates = [float(x) for x in args.serve_rates.split(",")]
@@ -383,9 +393,13 @@ def run_serve_mode(args, hs, torch, emit=True):
             tickets.append(srv.submit(gi, q))
         lats = []
         for t, a in zip(tickets, alone):
-            ids, gains, r, lat = srv.poll(t)
-            lats.append(lat)
-            identical &= bool(np.array_equal(ids, a[0]) and np.array_equal(gains, a[1]) and same_result(r, a[2]))
+            try:
+                ids, gains, r, lat = srv.poll(t)
+                lats.append(lat)
+                identical &= bool(a[0] == 0 and np.array_equal(ids, a[1]) and np.array_equal(gains, a[2]) and
+                                  same_result(r, a[3]))
+            except hs.HsawError as e:  # the same status as alone (an attempt budget that ran out)
+                identical &= bool(e.status == a[0])
         t_end = time.perf_counter()
         srv.close()
         per_rate.append({"offered_qps": rate, "solves_per_s": len(queries) / (t_end - t_start),
@@ -400,7 +414,9 @@ def run_serve_mode(args, hs, torch, emit=True):
                        "queries_per_rate": len(queries), "sources": [args.serve_min_sources, 1000], "k": [10, 1000],
                        "eps": [0.1, 0.2], "workers": args.serve_workers, "walk_pool_attempts": pool_sizes,
                        "walk_pool_build_s": pool_s, "walk_pool_gb": round(pool_gb, 2),
-                       "walk_seed": "shared per graph" if pool_attempts else "per query"},
+                       "walk_seed": "shared per graph" if pool_attempts else "per query",
+                       "max_attempts_per_query": int(args.serve_max_attempts) or None},
+            "queries_over_budget": sum(1 for a in alone if a[0] != 0),
             "serial_solves_per_s": serial_rate, "served_vs_serial": best["solves_per_s"] / serial_rate,
             "serial_pooled_solves_per_s": serial_pooled, "serial_pooled_device_ms_by_phase": serial_pooled_phase,
             "per_rate": per_rate, "identical_to_alone": bool(identical), "clocks": ck}
@@ -496,6 +512,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=16)
     ap.add_argument("--serve-min-sources", type=int, default=16)
     ap.add_argument("--serve-pool-attempts", type=float, default=536870912)
+    ap.add_argument("--serve-max-attempts", type=float, default=0)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

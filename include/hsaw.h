@@ -53,7 +53,8 @@ typedef enum {
   HSAW_E_STEP_CAP = -6,    /* a walk exceeded its step guard (cannot happen for valid graphs) */
   HSAW_E_TIMEOUT = -7,     /* attempt budget exhausted before enough walks hit */
   HSAW_E_REJECTED = -8,    /* server admission refused the query */
-  HSAW_E_CANCELLED = -9    /* query cancelled */
+  HSAW_E_CANCELLED = -9,   /* query cancelled */
+  HSAW_E_PENDING = -10     /* server poll: the query is still running (the ticket stays valid) */
 } hsaw_status;
 
 typedef enum { HSAW_EDGE = 0 /* eSI */, HSAW_NODE = 1 /* nSI */ } hsaw_mode;
@@ -189,7 +190,7 @@ HSAW_API hsaw_status hsaw_debug_fail_alloc_after(int64_t n);
  *   arrays and returns a ticket; a query whose estimate alone exceeds the budget is
  *   refused with HSAW_E_REJECTED.  Queries start in submission order as soon as a worker
  *   is free and the budget has room, while earlier ones are still running.
- *   hsaw_server_poll waits up to timeout_ms (< 0: forever) for the ticket: HSAW_E_TIMEOUT
+ *   hsaw_server_poll waits up to timeout_ms (< 0: forever) for the ticket: HSAW_E_PENDING
  *   if still running (the ticket stays valid), else the query's own status, with r
  *   filled as by hsaw_solve and *latency_ms (may be NULL) = completion - submission;
  *   the ticket is then released.  hsaw_server_cancel: a queued query never starts, a

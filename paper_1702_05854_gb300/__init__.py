@@ -21,7 +21,7 @@ from . import build as _build
 HSAW_OK = 0
 STATUS = {0: "HSAW_OK", -1: "HSAW_E_INVALID", -2: "HSAW_E_WEIGHT_SUM", -3: "HSAW_E_RANGE", -4: "HSAW_E_NOMEM",
           -5: "HSAW_E_DEVICE", -6: "HSAW_E_STEP_CAP", -7: "HSAW_E_TIMEOUT", -8: "HSAW_E_REJECTED",
-          -9: "HSAW_E_CANCELLED"}
+          -9: "HSAW_E_CANCELLED", -10: "HSAW_E_PENDING"}
 HSAW_EDGE, HSAW_NODE = 0, 1
 HSAW_FIXED_N, HSAW_STOP_RULE = 0, 1
 HSAW_INPUT_DEVICE = 1
@@ -330,8 +330,9 @@ class Server:
         return int(t.value)
 
     def poll(self, ticket: int, timeout_ms: int = -1):
-        """(ids, gains, result dict, latency_ms); raises HsawError (HSAW_E_TIMEOUT while running)."""
-        k = self._k[ticket]
+        """(ids, gains, result dict, latency_ms); raises HsawError (HSAW_E_PENDING while running,
+        else the query's own failing status)."""
+        k = self._k.get(ticket, 1)  # an unknown ticket: the library reports HSAW_E_INVALID
         ids = np.empty(k, np.int64)
         gains = np.empty(k, np.uint32)
         r = hsaw_result()
@@ -339,7 +340,7 @@ class Server:
         r.gains = _ptr(gains)
         lat = _dbl()
         rc = load().hsaw_server_poll(self._h, ticket, ctypes.byref(r), timeout_ms, ctypes.byref(lat))
-        if rc != -7:
+        if rc != -10:
             self._k.pop(ticket, None)
         _check(rc)
         return ids, gains, _result_dict(r), lat.value

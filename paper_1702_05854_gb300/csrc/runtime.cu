@@ -277,7 +277,7 @@ hsaw_status hsaw_server_poll(hsaw_server h, uint64_t ticket, hsaw_result* r, int
   if (timeout_ms < 0) {
     S.cv_done.wait(lk, ready);
   } else if (!S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
-    return fail(HSAW_E_TIMEOUT, "server: query still running");
+    return fail(HSAW_E_PENDING, "server: query still running");
   }
   S.tickets.erase(it);
   lk.unlock();

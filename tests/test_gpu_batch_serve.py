@@ -134,7 +134,15 @@ def test_server_poll_timeout_keeps_ticket():
     t = srv.submit(0, q)
     with pytest.raises(hs.HsawError) as e:
         srv.poll(t, timeout_ms=0)
-    assert e.value.status == -7
+    assert e.value.status == -10  # HSAW_E_PENDING: still running, ticket kept
     ids, gains, r, lat = srv.poll(t)
     assert r["hits"] == 300 and ids[0] == 12345
+    # a query whose own attempt budget runs out reports HSAW_E_TIMEOUT, and its ticket is gone
+    t2 = srv.submit(0, hs.Query(sources=S, mode=hs.HSAW_NODE, k=1, n_hsaw=300, seed=9, max_attempts=1 << 20))
+    with pytest.raises(hs.HsawError) as e:
+        srv.poll(t2)
+    assert e.value.status == -7
+    with pytest.raises(hs.HsawError) as e:
+        srv.poll(t2, timeout_ms=0)
+    assert e.value.status == -1  # unknown ticket
     srv.close()
