@@ -227,6 +227,10 @@ HSAW_API hsaw_status hsaw_walks_info(hsaw_walks w, int64_t* count, int64_t* tota
                             uint64_t* steps);
 HSAW_API hsaw_status hsaw_walks_export(hsaw_walks w, uint64_t* aid, int64_t* node_off, int32_t* nodes, int32_t* edges,
                               void* stream);
+/* The same arrays copied on the device, stream-ordered, into caller-owned device buffers of
+ * the walks' device (any NULL; sizes as for hsaw_walks_export).  Synchronises `stream`. */
+HSAW_API hsaw_status hsaw_walks_export_device(hsaw_walks w, uint64_t* aid_dev, int64_t* node_off_dev,
+                                              int32_t* nodes_dev, int32_t* edges_dev, void* stream);
 HSAW_API hsaw_status hsaw_walks_destroy(hsaw_walks w);
 
 /* Per-attempt outcome of attempts [first, first + count) (device buffers from the caller):

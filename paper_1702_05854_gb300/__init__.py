@@ -63,6 +63,7 @@ SIGNATURES = {
     "hsaw_walks_info": (ctypes.c_int, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_u64),
                                        ctypes.POINTER(_u64)]),
     "hsaw_walks_export": (ctypes.c_int, [_p, _p, _p, _p, _p, _p]),
+    "hsaw_walks_export_device": (ctypes.c_int, [_p, _p, _p, _p, _p, _p]),
     "hsaw_walks_destroy": (ctypes.c_int, [_p]),
     "hsaw_classify": (ctypes.c_int, [_p, ctypes.POINTER(hsaw_query), _u64, _i64, _p, _p, _p]),
     "hsaw_histogram": (ctypes.c_int, [_p, ctypes.c_int, _i64, _i64, _p, _p, _i64, ctypes.POINTER(_i64), _p]),
@@ -390,6 +391,20 @@ class Walks:
         nodes = np.empty(tot, np.int32)
         edges = np.empty(max(tot - cnt, 0), np.int32)
         _check(load().hsaw_walks_export(self._h, _ptr(aid), _ptr(off), _ptr(nodes), _ptr(edges), _stream(stream)))
+        return aid, off, nodes, edges
+
+    def export_device(self, stream=None):
+        """The same arrays as export(), as torch CUDA tensors (aid as int64 bits of uint64),
+        copied on the device into caller-owned buffers."""
+        import torch
+        inf = self.info()
+        cnt, tot = inf["count"], inf["total_nodes"]
+        aid = torch.empty(cnt, dtype=torch.int64, device="cuda")
+        off = torch.empty(cnt + 1, dtype=torch.int64, device="cuda")
+        nodes = torch.empty(tot, dtype=torch.int32, device="cuda")
+        edges = torch.empty(max(tot - cnt, 0), dtype=torch.int32, device="cuda")
+        _check(load().hsaw_walks_export_device(self._h, _ptr(aid), _ptr(off), _ptr(nodes), _ptr(edges),
+                                               _stream(stream)))
         return aid, off, nodes, edges
 
 

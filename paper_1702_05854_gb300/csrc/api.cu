@@ -299,6 +299,21 @@ hsaw_status hsaw_walks_export(hsaw_walks w, uint64_t* aid, int64_t* node_off, in
   return HSAW_OK;
 }
 
+hsaw_status hsaw_walks_export_device(hsaw_walks w, uint64_t* aid, int64_t* node_off, int32_t* nodes, int32_t* edges,
+                                     void* stream) {
+  if (!w) return fail(HSAW_E_INVALID, "walks: NULL handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Stream& st = w->st;
+  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+  if (aid && st.count) HSAW_CK(cudaMemcpyAsync(aid, st.aid.p, (size_t)st.count * 8, dd, s));
+  if (node_off) HSAW_CK(cudaMemcpyAsync(node_off, st.node_off.p, (size_t)(st.count + 1) * 8, dd, s));
+  if (nodes && st.total_nodes) HSAW_CK(cudaMemcpyAsync(nodes, st.nodes.p, (size_t)st.total_nodes * 4, dd, s));
+  if (edges && st.total_nodes > st.count)
+    HSAW_CK(cudaMemcpyAsync(edges, st.edges.p, (size_t)(st.total_nodes - st.count) * 4, dd, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  return HSAW_OK;
+}
+
 hsaw_status hsaw_walks_destroy(hsaw_walks w) {
   if (!w) return HSAW_OK;
   cudaDeviceSynchronize();

@@ -123,3 +123,13 @@ def test_profile_counters_reset_and_results_unchanged(c1):
     hs.hsaw_profile_enable(False)
     p = hs.hsaw_profile_read()
     assert p["kernel_launches"] == 0 and p["sampler_launches"] == 0 and p["phase_ms"]["greedy"] == 0
+
+
+def test_walks_export_device_equals_host(c1):
+    """Device export into caller-owned torch tensors gives the host export's arrays."""
+    d, g = c1[0], c1[1]
+    w = hs.hsaw_sample(g, hs.Query(sources=d["sources"], k=1, seed=4), 100, 3000)
+    aid, off, nodes, edges = w.export()
+    daid, doff, dnodes, dedges = w.export_device()
+    assert np.array_equal(daid.cpu().numpy().view(np.uint64), aid) and np.array_equal(doff.cpu().numpy(), off)
+    assert np.array_equal(dnodes.cpu().numpy(), nodes) and np.array_equal(dedges.cpu().numpy(), edges)
