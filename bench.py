@@ -414,7 +414,9 @@ def run_serve_mode(args, hs, torch, emit=True):
                        "queries_per_rate": len(queries), "sources": [args.serve_min_sources, 1000], "k": [10, 1000],
                        "eps": [0.1, 0.2], "workers": args.serve_workers, "walk_pool_attempts": pool_sizes,
                        "walk_pool_build_s": pool_s, "walk_pool_gb": round(pool_gb, 2),
-                       "walk_seed": "shared per graph" if pool_attempts else "per query",
+                       "walk_seed": ("shared per graph: queries on a graph draw the same live-edge worlds, each "
+                                     "result is its own estimator, errors across queries correlate")
+                       if pool_attempts else "per query",
                        "max_attempts_per_query": int(args.serve_max_attempts) or None},
             "queries_over_budget": sum(1 for a in alone if a[0] != 0),
             "serial_solves_per_s": serial_rate, "served_vs_serial": best["solves_per_s"] / serial_rate,

@@ -518,10 +518,14 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
     if (cancel_requested()) return fail(HSAW_E_CANCELLED, "sampling: query cancelled");
     const uint64_t used = st.next_attempt - st.first_attempt;
     if (used >= st.max_attempts) return fail(HSAW_E_TIMEOUT, "sampling: attempt budget exhausted before enough hits");
-    // window size from the hit rate so far (2^20 .. 2^28 attempts; doubling while no hit)
+    // window size from the hit rate so far (2^20 .. 2^28 attempts; doubling while no hit),
+    // with a margin of 4 standard deviations of the rate estimate (st.count hits seen) and
+    // of the window's own hit count (need): attempts past the last hit a solve uses are
+    // wasted, and a window that falls short only costs one more launch
     const double need = (double)(want - st.count);
     st.hit_rate = used ? (double)st.count / (double)used : 0.0;
-    double target = st.hit_rate > 0 ? need / st.hit_rate * 1.05 + 4096.0 : std::max(1048576.0, 2.0 * (double)used);
+    const double margin = std::min(1.25, 1.0 + 4.0 / std::sqrt(std::max(1.0, (double)st.count)) + 4.0 / std::sqrt(need));
+    double target = st.hit_rate > 0 ? need / st.hit_rate * margin + 4096.0 : std::max(1048576.0, 2.0 * (double)used);
     target = std::max(target, 1048576.0);
     target = std::min(target, 268435456.0);
     uint64_t batch = (uint64_t)target;
