@@ -278,6 +278,24 @@ def run_batch_mode(args, hs, torch, emit=True):
     identical = all(st == 0 and np.array_equal(ids, a[0]) and np.array_equal(gains, a[1]) and same_result(r, a[2])
                     for (st, ids, gains, r), a in zip(batched, serial))
     n = len(inst)
+    breakdown = None
+    if args.batch_profile:  # a third, profiled serial pass: per-instance time and sampler time
+        per = []
+        for x, g, q in zip(inst, graphs, queries):
+            hs.hsaw_profile_enable(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hs.hsaw_solve(g, q)
+            torch.cuda.synchronize()
+            p = hs.hsaw_profile_read()
+            per.append({"n": x["n"], "m": x["m"], "sources": len(x["sources"]), "k": x["k"], "mode": x["mode"],
+                        "s": time.perf_counter() - t0, "sampler_s": p["sampler_ms"] / 1e3,
+                        "draws": p["sampler_steps"]})
+        hs.hsaw_profile_enable(False)
+        tot, samp = sum(r["s"] for r in per), sum(r["sampler_s"] for r in per)
+        per.sort(key=lambda r: -r["s"])
+        breakdown = {"serial_s": tot, "sampler_s": samp, "sampler_share": samp / tot, "bound_batched_vs_serial":
+                     tot / samp, "slowest": per[:15], "under_50ms": sum(1 for r in per if r["s"] < 0.05)}
     line = {"metric": f"batched SI solves/s ({n} Chung-Lu eSI/nSI instances, N={args.batch_nhsaw} HSAWs each)",
             "value": n / t_batch, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -287,7 +305,8 @@ def run_batch_mode(args, hs, torch, emit=True):
                        "workers": args.batch_workers, "graph_gen_s": gen_s,
                        "edges_total": int(sum(x["m"] for x in inst))},
             "serial_solves_per_s": n / t_serial, "batched_vs_serial": t_serial / t_batch,
-            "identical_to_serial": bool(identical), "gpu_launches": prof["kernel_launches"], "clocks": ck}
+            "identical_to_serial": bool(identical), "gpu_launches": prof["kernel_launches"], "clocks": ck,
+            "serial_profile": breakdown}
     if emit:
         print(json.dumps(line), flush=True)
     return line
@@ -508,6 +527,7 @@ def main():
     ap.add_argument("--batch-nmax", type=float, default=1e6)
     ap.add_argument("--batch-nhsaw", type=int, default=100_000)
     ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--batch-profile", action="store_true", help="add a profiled serial pass (per-instance times)")
     ap.add_argument("--serve-scales", default="18,20")
     ap.add_argument("--serve-queries", type=int, default=200)
     ap.add_argument("--serve-rates", default="10,30,100,300,1000,2000")
