@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -578,6 +579,151 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
   if (rank == 0 && threadIdx.x == 0) P.ctl[3] = (uint32_t)r;
 }
 
+// ------------------------------------------------------------------ greedy with on-chip counts
+// When the running counts and inverted-index offsets of all touched elements fit in the
+// cluster's shared memory (about 26 K elements per CTA), CTA r owns elements
+// [r * per, (r + 1) * per): their counts, their walk-list offsets, and the largest key of
+// each 32-element group, all in its shared memory.  A CTA's candidate for the argmax
+// carries its walk-list range, so once the winner is known every CTA starts covering
+// without a global-memory lookup; decrements are atomics on the owner's shared memory
+// (distributed shared memory), with the stale mark as in k_greedy_cluster; rescans read
+// shared memory only.
+struct OnchipGreedyParams {
+  uint32_t U, per;        // elements, elements per CTA
+  uint32_t short_walks;
+  int32_t k;
+  const uint32_t* cnt0;   // initial counts | EXCLUDED (U)
+  const uint32_t* inv_off;  // U + 1
+  const uint4* inv_ent;
+  const uint32_t* entry_uidx;
+  uint8_t* covered;
+  uint32_t* out_u;
+  uint32_t* out_gain;
+  uint32_t* ctl;  // [3] rounds done
+};
+
+constexpr uint32_t ONCHIP_GROUP = 32;
+
+__device__ __forceinline__ void onchip_decrement(const OnchipGreedyParams& P, cg::cluster_group& cluster,
+                                                 uint32_t* cnt_s, unsigned long long* gkey, uint32_t* sbits,
+                                                 uint32_t x) {
+  const uint32_t owner = x / P.per, lx = x - owner * P.per, gl = lx / ONCHIP_GROUP;
+  atomicSub(cluster.map_shared_rank(&cnt_s[lx], owner), 1u);
+  const unsigned long long top = *cluster.map_shared_rank(&gkey[gl], owner);
+  if (top != 0 && 0xFFFFFFFFu - (uint32_t)top == x)
+    atomicOr(cluster.map_shared_rank(&sbits[gl >> 5], owner), 1u << (gl & 31));
+}
+
+__global__ void __launch_bounds__(1024, 1) k_greedy_onchip(OnchipGreedyParams P) {
+  extern __shared__ unsigned long long smem_u64[];
+  __shared__ unsigned long long red[32];
+  __shared__ unsigned long long slot_key[16];
+  __shared__ unsigned long long slot_rng[16];  // walk-list range (q0 << 32 | q1) of each CTA's candidate
+  cg::cluster_group cluster = cg::this_cluster();
+  const uint32_t rank = cluster.block_rank();
+  const uint32_t C = cluster.num_blocks();
+  const uint32_t per = P.per;
+  const uint32_t ng = (per + ONCHIP_GROUP - 1) / ONCHIP_GROUP;
+  const uint32_t words = (ng + 31) / 32;
+  unsigned long long* gkey = smem_u64;                       // ng
+  uint32_t* cnt_s = reinterpret_cast<uint32_t*>(gkey + ng);  // per
+  uint32_t* off_s = cnt_s + per;                             // per + 1
+  uint32_t* sbits = off_s + per + 1;                         // words
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t base = rank * per;
+  const uint32_t own = P.U > base ? min(per, P.U - base) : 0;
+  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) cnt_s[i] = i < own ? P.cnt0[base + i] : EXCLUDED;
+  for (uint32_t i = threadIdx.x; i <= own; i += blockDim.x) off_s[i] = P.inv_off[base + i];
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sbits[i] = 0xFFFFFFFFu;
+  for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) gkey[i] = 0;
+  cluster.sync();
+  int32_t r = 0;
+  for (; r < P.k; ++r) {
+    // 1. rescan the stale groups from shared memory, one warp per group, one element per lane
+    for (uint32_t wi = w; wi < words; wi += nw) {
+      uint32_t todo = sbits[wi];
+      __syncwarp();
+      if (!todo) continue;
+      if (lane == 0) sbits[wi] = 0;
+      while (todo) {
+        const uint32_t gl = wi * 32 + __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t lx = gl * ONCHIP_GROUP + lane;
+        unsigned long long key = lx < per ? elem_key(cnt_s[lx], base + lx) : 0ull;
+        key = warp_max_u64(key);
+        if (lane == 0 && gl < ng) gkey[gl] = key;
+      }
+    }
+    __syncthreads();
+    // 2. this CTA's candidate with its walk-list range, pushed into every CTA's slots
+    unsigned long long key = 0;
+    for (uint32_t gl = threadIdx.x; gl < ng; gl += blockDim.x) key = gkey[gl] > key ? gkey[gl] : key;
+    key = warp_max_u64(key);
+    if (lane == 0) red[w] = key;
+    __syncthreads();
+    if (w == 0) {
+      key = lane < nw ? red[lane] : 0ull;
+      key = warp_max_u64(key);
+      unsigned long long rng = 0;
+      if (key) {
+        const uint32_t lx = 0xFFFFFFFFu - (uint32_t)key - base;
+        rng = ((unsigned long long)off_s[lx] << 32) | off_s[lx + 1];
+      }
+      if (lane < (int)C) {
+        *cluster.map_shared_rank(&slot_key[rank], lane) = key;
+        *cluster.map_shared_rank(&slot_rng[rank], lane) = rng;
+      }
+    }
+    cluster.sync();
+    key = lane < (int)C ? slot_key[lane] : 0ull;
+    const unsigned long long best = warp_max_u64(key);
+    const uint32_t gain = (uint32_t)(best >> 32);
+    if (gain == 0) break;  // every remaining gain is zero: the same decision in every CTA
+    const uint32_t u = 0xFFFFFFFFu - (uint32_t)best;
+    const uint32_t winner = u / per;
+    const unsigned long long rng = slot_rng[winner];
+    const uint32_t q0 = (uint32_t)(rng >> 32), q1 = (uint32_t)rng;
+    if (rank == 0 && threadIdx.x == 0) {
+      P.out_u[r] = u;
+      P.out_gain[r] = gain;
+    }
+    if (rank == winner && threadIdx.x == 0) {  // the picked element leaves the candidates
+      const uint32_t lx = u - base;
+      atomicOr(&cnt_s[lx], EXCLUDED);
+      atomicOr(&sbits[(lx / ONCHIP_GROUP) >> 5], 1u << ((lx / ONCHIP_GROUP) & 31));
+    }
+    // 3. cover its walks; the group keys read by onchip_decrement do not change until step 1
+    if (P.short_walks) {
+      for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
+        const uint4 ent = __ldg(&P.inv_ent[q]);
+        const uint32_t x0 = ent.y < ent.z ? __ldg(&P.entry_uidx[ent.y]) : 0u;  // in flight with the flag
+        if (__ldcg(&P.covered[ent.x])) continue;
+        P.covered[ent.x] = 1;
+        if (ent.y < ent.z) onchip_decrement(P, cluster, cnt_s, gkey, sbits, x0);
+        for (uint32_t p = ent.y + 1; p < ent.z; ++p)
+          onchip_decrement(P, cluster, cnt_s, gkey, sbits, __ldg(&P.entry_uidx[p]));
+      }
+    } else {
+      for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
+        const uint4 ent = __ldg(&P.inv_ent[q]);
+        const uint32_t p = ent.y + lane;
+        const uint32_t x = p < ent.z ? __ldg(&P.entry_uidx[p]) : 0u;  // in flight with the flag
+        uint32_t fresh = 0;
+        if (lane == 0) fresh = __ldcg(&P.covered[ent.x]) ? 0u : 1u;
+        fresh = __shfl_sync(0xffffffffu, fresh, 0);
+        if (!fresh) continue;
+        if (lane == 0) P.covered[ent.x] = 1;
+        if (p < ent.z) onchip_decrement(P, cluster, cnt_s, gkey, sbits, x);
+        for (uint32_t pp = p + 32; pp < ent.z; pp += 32)
+          onchip_decrement(P, cluster, cnt_s, gkey, sbits, __ldg(&P.entry_uidx[pp]));
+      }
+    }
+    cluster.sync();
+  }
+  cluster.sync();  // no CTA leaves while a peer may still read its shared memory
+  if (rank == 0 && threadIdx.x == 0) P.ctl[3] = (uint32_t)r;
+}
+
 // Inverted-index entries with their walk's entry range: {j, walk_eoff[j], walk_eoff[j + 1], 0}.
 __global__ void k_inv_ranges(const uint32_t* __restrict__ inv_walk, const uint32_t* __restrict__ walk_eoff, uint32_t E,
                              uint4* __restrict__ inv_ent) {
@@ -645,54 +791,137 @@ static int greedy_grid() {
   return cached;
 }
 
+// The largest cluster (16 CTAs, else 8) that a 1024-thread greedy kernel with the full
+// opt-in shared memory can run on, and that memory less room for its static arrays.
+struct ClusterCfg {
+  int size = 0;
+  size_t smem_cap = 0;
+};
+
+template <class Kernel>
+static ClusterCfg cluster_cfg_for(Kernel kernel) {
+  ClusterCfg c;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  c.smem_cap = optin > 16384 ? (size_t)optin - 12288 : 0;  // keep room for the static shared arrays
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_cap) != cudaSuccess) {
+    cudaGetLastError();
+    return c;
+  }
+  const int want[2] = {16, 8};
+  for (int i = 0; i < 2 && !c.size; ++i) {
+    if (want[i] > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = want[i];
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(want[i]);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = c.smem_cap;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) == cudaSuccess && nclusters > 0)
+      c.size = want[i];
+    else
+      cudaGetLastError();
+  }
+  return c;
+}
+
+// The greedy with on-chip counts when one cluster's shared memory holds every touched
+// element's count and walk-list offsets; *done = false leaves the other versions to run.
+static hsaw_status onchip_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k, uint32_t* outs, uint32_t* ctl,
+                                 uint32_t csize, bool short_walks, int32_t* rounds, bool* done, cudaStream_t s) {
+  static const ClusterCfg cfg1 = cluster_cfg_for(k_greedy_onchip);
+  if (!cfg1.size) return HSAW_OK;
+  const uint32_t U = (uint32_t)cv.unique;
+  auto need = [](uint32_t per) {
+    const size_t ng = (per + ONCHIP_GROUP - 1) / ONCHIP_GROUP;
+    return ng * 8 + (size_t)per * 4 + ((size_t)per + 1) * 4 + (ng + 31) / 32 * 4 + 64;
+  };
+  auto per_for = [U](uint32_t c) { return (uint32_t)(((uint64_t)U + c - 1) / c + 31) / 32 * 32; };
+  csize = std::min<uint32_t>(std::max<uint32_t>(csize, 1), (uint32_t)cfg1.size);
+  while (need(per_for(csize)) > cfg1.smem_cap && (int)csize < cfg1.size) csize *= 2;
+  const uint32_t per = per_for(csize);
+  if (need(per) > cfg1.smem_cap) return HSAW_OK;
+  HSAW_TRY(cv.cnt_work.ensure(U, s));
+  HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
+  HSAW_TRY(cv.inv_ent.ensure((size_t)cv.entries, s));
+  HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
+  count_launch();
+  k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);
+  HSAW_CK(cudaGetLastError());
+  count_launch();
+  k_inv_ranges<<<grid_for((size_t)cv.entries, 256, 8192), 256, 0, s>>>(cv.inv_walk.p, cv.walk_eoff.p,
+                                                                      (uint32_t)cv.entries, cv.inv_ent.p);
+  HSAW_CK(cudaGetLastError());
+  OnchipGreedyParams P;
+  P.U = U;
+  P.per = per;
+  P.short_walks = short_walks ? 1u : 0u;
+  P.k = k;
+  P.cnt0 = cv.cnt_work.p;
+  P.inv_off = cv.inv_off.p;
+  P.inv_ent = cv.inv_ent.p;
+  P.entry_uidx = cv.entry_uidx.p;
+  P.covered = cv.covered.p;
+  P.out_u = outs;
+  P.out_gain = outs + k;
+  P.ctl = ctl;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = need(per);
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const bool log = getenv("HSAW_LOG_LAUNCHES") != nullptr;  // measurement aid
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (log) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, s);
+  }
+  count_launch();
+  HSAW_CK(cudaLaunchKernelEx(&cfg, k_greedy_onchip, P));
+  uint32_t h[4];
+  HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
+  if (log) cudaEventRecord(ev1, s);
+  HSAW_CK(cudaStreamSynchronize(s));
+  if (log) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    fprintf(stderr, "hsaw: k_greedy_onchip walks=%lld entries=%lld unique=%u cluster=%u per=%u k=%d ms=%.3f\n",
+            (long long)cv.walks, (long long)cv.entries, U, csize, per, k, ms);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  *rounds = (int32_t)h[3];
+  *done = true;
+  return HSAW_OK;
+}
+
 // Launch the cluster greedy when one cluster's shared memory holds the group maxima;
-// *done = false leaves the grid-wide version to run.
+// *done = false leaves the grid-wide version to run.  HSAW_GREEDY=grid selects the grid-wide
+// version, HSAW_GREEDY=cluster the cluster version with counts in global memory (tests).
 static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k, uint32_t* outs, uint32_t* ctl,
                                   int32_t* rounds, bool* done, cudaStream_t s) {
   *done = false;
-  const char* force = getenv("HSAW_GREEDY");  // "grid" selects the grid-wide version (tests)
+  const char* force = getenv("HSAW_GREEDY");
   if (force && force[0] == 'g') return HSAW_OK;
-  struct ClusterCfg {
-    int size = 0;
-    size_t smem_cap = 0;
-  };
-  static const ClusterCfg cfg0 = [] {
-    ClusterCfg c;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    c.smem_cap = optin > 16384 ? (size_t)optin - 12288 : 0;  // keep room for the static shared arrays
-    if (cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_cap) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return c;
-    }
-    const int want[2] = {16, 8};
-    for (int i = 0; i < 2 && !c.size; ++i) {
-      if (want[i] > 8 &&
-          cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = want[i];
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(want[i]);
-      cfg.blockDim = dim3(1024);
-      cfg.dynamicSmemBytes = c.smem_cap;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int nclusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclusters, k_greedy_cluster, &cfg) == cudaSuccess && nclusters > 0)
-        c.size = want[i];
-      else
-        cudaGetLastError();
-    }
-    return c;
-  }();
+  static const ClusterCfg cfg0 = cluster_cfg_for(k_greedy_cluster);
   const int cluster_size = cfg0.size;
   const size_t smem_cap = cfg0.smem_cap;
   if (!cluster_size) return HSAW_OK;
@@ -707,6 +936,10 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   const uint64_t walks = (uint64_t)cv.walks;
   const bool short_walks = walks > 0 && (uint64_t)cv.entries < 8ull * walks;
   while ((int)csize < cluster_size && ((uint64_t)csize << 14) < (uint64_t)cv.entries) csize *= 2;
+  if (!(force && strcmp(force, "cluster") == 0)) {
+    HSAW_TRY(onchip_greedy(cv, cand_dev, k, outs, ctl, csize, short_walks, rounds, done, s));
+    if (*done) return HSAW_OK;
+  }
   per = (NG + csize - 1) / csize;
   while (need(per) > smem_cap && (int)csize < cluster_size) {
     csize *= 2;

@@ -4,8 +4,10 @@ Two streams of N = 100,000 HSAWs on R-MAT scale 22 (4,194,304 nodes, 67,108,864 
 eSI with weighted-cascade weights and 4,000 sources (about 6.8 M walk edges, 6.4 M of
 them distinct), and nSI with random LT weights and 20,000 sources.  k = 1,000 picks are
 compared id by id and gain by gain with the oracle's greedy over the oracle's own stream,
-once on the cluster greedy (checked from its launch record to run on at least 8 CTAs
-with more than one element group per CTA) and once on the grid-wide fallback.  The
+on the cluster greedy with on-chip counts (the nSI stream; the eSI stream's 6.4 M
+elements do not fit on chip), on the cluster greedy with counts in global memory (both;
+each checked from its launch record to run on at least 8 CTAs with more than one element
+group per CTA), and on the grid-wide fallback.  The
 oracle draws the stream on all host cores (consecutive attempt ranges joined in order)
 and runs the greedy that keeps its gains, which the CPU tests hold equal to the
 recounting greedy.
@@ -31,7 +33,8 @@ CASES = {
     "esi-wc-4000": dict(weights="wc", n_sources=4000, mode="edge"),
     "nsi-random-20000": dict(weights="random", n_sources=20000, mode="node"),
 }
-LOG = re.compile(r"k_greedy_cluster walks=(\d+) entries=(\d+) unique=(\d+) cluster=(\d+) gshift=(\d+) k=(\d+)")
+LOG = re.compile(r"k_greedy_(cluster|onchip) walks=(\d+) entries=(\d+) unique=(\d+) cluster=(\d+) (gshift|per)=(\d+) "
+                 r"k=(\d+)")
 
 
 @pytest.fixture(scope="module", params=list(CASES))
@@ -51,15 +54,15 @@ def case(request):
     q = hs.Query(sources=d["sources"], mode=hs.HSAW_EDGE if c["mode"] == "edge" else hs.HSAW_NODE, k=K, n_hsaw=N,
                  seed=synth.SEED_WALKS)
     return dict(g=g, q=q, oids=oids, ogains=ogains, attempts=int(W.aid[N - 1]) + 1,
-                entries=int(W.elements(omode)[0].shape[0]))
+                entries=int(W.elements(omode)[0].shape[0]), esi=c["mode"] == "edge")
 
 
-def _solve(case, capfd, monkeypatch, grid):
+def _solve(case, capfd, monkeypatch, variant):
     monkeypatch.setenv("HSAW_LOG_LAUNCHES", "1")
-    if grid:
-        monkeypatch.setenv("HSAW_GREEDY", "grid")
-    else:
+    if variant == "default":
         monkeypatch.delenv("HSAW_GREEDY", raising=False)
+    else:
+        monkeypatch.setenv("HSAW_GREEDY", variant)
     capfd.readouterr()
     ids, gains, r = hs.hsaw_solve(case["g"], case["q"])
     return ids, gains, r, capfd.readouterr().err
@@ -73,18 +76,26 @@ def _same_as_oracle(case, ids, gains, r):
     assert case["ogains"][-1] > 0  # every pick is a real argmax, not a zero-gain fill
 
 
-def test_cluster_greedy_matches_oracle_at_scale(case, capfd, monkeypatch):
-    ids, gains, r, err = _solve(case, capfd, monkeypatch, grid=False)
+@pytest.mark.parametrize("variant", ["default", "cluster"])
+def test_cluster_greedy_matches_oracle_at_scale(case, capfd, monkeypatch, variant):
+    """default: on-chip counts when they fit the cluster (the nSI stream), else counts in
+    global memory (the eSI stream); cluster: counts in global memory for both."""
+    ids, gains, r, err = _solve(case, capfd, monkeypatch, variant)
     m = LOG.search(err)
     assert m, err[-2000:]
-    walks, entries, unique, csize, gshift, k = (int(x) for x in m.groups())
+    kind, walks, entries, unique, csize, what, size, k = m.groups()
+    walks, entries, unique, csize, size, k = (int(x) for x in (walks, entries, unique, csize, size, k))
     assert walks == N and entries == case["entries"] and k == K
-    groups = math.ceil(unique / (1 << gshift))
-    assert csize >= 8 and math.ceil(groups / csize) > 1  # the multi-CTA paths ran
+    if kind == "onchip":
+        groups_per_cta = math.ceil(size / 32)
+    else:
+        groups_per_cta = math.ceil(math.ceil(unique / (1 << size)) / csize)
+    assert csize >= 8 and groups_per_cta > 1  # the multi-CTA paths ran
+    assert kind == ("cluster" if variant == "cluster" or case["esi"] else "onchip")
     _same_as_oracle(case, ids, gains, r)
 
 
 def test_grid_greedy_matches_oracle_at_scale(case, capfd, monkeypatch):
-    ids, gains, r, err = _solve(case, capfd, monkeypatch, grid=True)
-    assert "k_greedy_cluster" not in err
+    ids, gains, r, err = _solve(case, capfd, monkeypatch, "grid")
+    assert "k_greedy_cluster" not in err and "k_greedy_onchip" not in err
     _same_as_oracle(case, ids, gains, r)

@@ -214,9 +214,12 @@ def test_greedy_matches_oracle(c1_stream, mode, k):
     assert np.array_equal(ids, oids) and np.array_equal(gains, ogains)
 
 
-def test_greedy_grid_version_matches_oracle(c1_stream, monkeypatch):
-    """The grid-wide greedy (used when a cluster cannot hold the group maxima) agrees too."""
-    monkeypatch.setenv("HSAW_GREEDY", "grid")
+@pytest.mark.parametrize("variant", ["grid", "cluster"])
+def test_greedy_other_versions_match_oracle(c1_stream, monkeypatch, variant):
+    """The grid-wide greedy (used when a cluster cannot hold the group maxima) and the
+    cluster greedy with counts in global memory (used when on-chip counts do not fit)
+    agree too; by default these C1 sizes run the greedy with on-chip counts."""
+    monkeypatch.setenv("HSAW_GREEDY", variant)
     d, g, og, w, st = c1_stream
     for mode, M, k in ((hs.HSAW_EDGE, d["m"], 40), (hs.HSAW_NODE, d["n"], 25)):
         ids, gains = hs.hsaw_greedy(w, g, mode, 100, 15_000, k)
