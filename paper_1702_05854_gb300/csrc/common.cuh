@@ -104,10 +104,8 @@ struct Graph {
   int device = 0;
 };
 
-// Sampler occupancy autotuner state of a graph (sample.cu): forget it when the graph goes;
-// the tuned blocks per SM, 0 while still tuning.
+// Sampler occupancy autotuner state of a graph (sample.cu): forget it when the graph goes.
 void sample_tune_forget(const Graph& g);
-int sample_tuned_blocks(const Graph& g);
 
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, SC'11: 10 rounds of two 32x32->64 multiplies with the

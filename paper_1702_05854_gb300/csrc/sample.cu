@@ -379,12 +379,6 @@ void sample_tune_forget(const Graph& g) {
   g_stune.erase(g.node);
 }
 
-int sample_tuned_blocks(const Graph& g) {
-  std::lock_guard<std::mutex> lk(g_stune_mu);
-  auto it = g_stune.find(g.node);
-  return it == g_stune.end() ? 0 : it->second.best;
-}
-
 // Blocks per SM for the next launch over `batch` attempts; *trial >= 0 when it is a timed trial.
 static int sample_blocks_for(const Graph& g, uint64_t batch, int* trial) {
   *trial = -1;
