@@ -122,6 +122,30 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same generator with its ten round keys (key + i * the Weyl constants, i = 0..9)
+// computed once per launch: a kernel that keeps them in its parameters (constant bank)
+// saves the two key additions of every round.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+inline PhiloxKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys K;
+  for (int i = 0; i < 10; ++i) {
+    K.k0[i] = k0 + (uint32_t)i * 0x9E3779B9u;
+    K.k1[i] = k1 + (uint32_t)i * 0xBB67AE85u;
+  }
+  return K;
+}
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ K.k0[i], lo1, hi0 ^ c.w ^ K.k1[i], lo0);
+  }
+  return c;
+}
+
 // Draw of node v in attempt a (one live-edge world per attempt).
 __device__ __forceinline__ uint4 node_draw(uint64_t a, uint32_t v, uint32_t k0, uint32_t k1) {
   return philox4x32_10(make_uint4((uint32_t)a, (uint32_t)(a >> 32), v, 0u), k0, k1);

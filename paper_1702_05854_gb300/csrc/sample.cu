@@ -46,10 +46,11 @@ struct SampleParams {
   uint32_t* chunk_hits;  // n_chunks
   uint2* recs;           // n_chunks * cap
   unsigned long long* steps;
+  PhiloxKeys keys;       // round keys of (k0, k1)
 };
 
 template <bool HAS_P, bool HAS_REM>
-__global__ void __launch_bounds__(256, 6) k_sample(SampleParams P) {
+__global__ void __launch_bounds__(256, 6) k_sample(const __grid_constant__ SampleParams P) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -77,7 +78,10 @@ __global__ void __launch_bounds__(256, 6) k_sample(SampleParams P) {
       const uint32_t rank = __popc(need & lt);
       if (!active && rank < avail) {
         off = cur + rank;
-        v = start_node(P.a0 + off, P.n, P.k0, P.k1);
+        {
+          const uint64_t a = P.a0 + off;
+          v = __umulhi(philox4x32_10_rk(make_uint4((uint32_t)a, (uint32_t)(a >> 32), 0u, 1u), P.keys).x, P.n);
+        }
         rec = __ldg(&P.node[v]);
         ck.reset(v);
         len = 1;
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(256, 6) k_sample(SampleParams P) {
       if (HAS_REM && len == 1 && P.node_removed && P.node_removed[v]) outcome = 0;
       if (outcome < 0) {
         const uint32_t sw = __ldg(&P.s_bits[v >> 5]);
-        const uint4 x = node_draw(a, v, P.k0, P.k1);
+        const uint4 x = philox4x32_10_rk(make_uint4((uint32_t)a, (uint32_t)(a >> 32), v, 0u), P.keys);
         const bool live = x.x < rec.w;
         uint4 ra = make_uint4(0, 0, 0, 0), rb = make_uint4(0, 0, 0, 0);
         uint32_t e = 0;
@@ -341,6 +345,7 @@ static SampleParams make_params(const Graph& g, const QueryDev& qd) {
   P.n = (uint32_t)g.n;
   P.k0 = (uint32_t)qd.seed;
   P.k1 = (uint32_t)(qd.seed >> 32);
+  P.keys = philox_round_keys(P.k0, P.k1);
   P.step_cap = (uint32_t)std::min<uint64_t>(4ull * (uint64_t)g.n + 64ull, 0xFFFFFFF0ull);
   return P;
 }
@@ -696,6 +701,7 @@ extern "C" hsaw_status hsaw_sample_hits_static(hsaw_graph g, const uint32_t* sus
   P.n = (uint32_t)G.n;
   P.k0 = (uint32_t)seed;
   P.k1 = (uint32_t)(seed >> 32);
+  P.keys = philox_round_keys(P.k0, P.k1);
   P.step_cap = (uint32_t)std::min<uint64_t>(4ull * (uint64_t)G.n + 64ull, 0xFFFFFFF0ull);
   const uint32_t n_chunks = (uint32_t)((n_attempts + STATIC_CHUNK - 1) / STATIC_CHUNK);
   P.a0 = first_attempt;
