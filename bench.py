@@ -39,8 +39,8 @@ BYTES_PER_STEP = 96  # three random 32-byte sectors per live-edge draw: node rec
 # DRAM bytes (read + write) per live-edge draw of the sampler kernel from an ncu capture,
 # keyed by (hash of the kernel's source, workload).  A workload without a capture of the
 # current kernel reports traffic = null.
-NCU_TRAFFIC = {("62b084bf844e", "rmat22-wc-eSI"): 122.9,   # profiles/k_sample_rmat22_dram.md
-               ("62b084bf844e", "rmat26-wc-eSI"): 122.9}   # the scale-22 figure, scaled by draws
+NCU_TRAFFIC = {("783e77c95bea", "rmat22-wc-eSI"): 122.9,   # profiles/k_sample_rmat22_dram.md
+               ("783e77c95bea", "rmat26-wc-eSI"): 122.9}   # the scale-22 figure, scaled by draws
 
 
 def sampler_hash():
