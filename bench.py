@@ -659,6 +659,10 @@ def main():
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["kernel_launches"],
         "clocks": ck,
     }
+    if cpu:  # the paper's convention (one core) and all host cores, as context
+        line["gpu_over_oracle"] = {"one_core": value / cpu["single_core"]["value"], "all_cores": value / cpu["value"],
+                                   "cores": cpu["cores"]}
+    roofline["attempts_per_s"] = prof["sampler_attempts"] / (prof["sampler_ms"] / 1e3) if prof["sampler_ms"] else 0.0
     if world == 1 and not args.no_extras:
         # the batched and served workloads, on the same GPU once the billion-edge graph is freed
         g.close()
