@@ -154,15 +154,23 @@ __global__ void __launch_bounds__(256) k_rs_hist(const uint32_t* __restrict__ ke
   counts[(size_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// One stable scatter pass.  The tile is first ordered by digit in shared memory (ranks
+// follow input order: warp sub-tiles in order, batches in order, lanes in order), then
+// written out in that order, so each digit's items leave as one contiguous run (about 16
+// items per digit and tile) instead of one scattered word per item.
 __global__ void __launch_bounds__(256) k_rs_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                                     size_t n, int shift, const uint32_t* __restrict__ offsets,
                                                     uint32_t tiles, uint32_t* __restrict__ keys_out,
                                                     uint32_t* __restrict__ vals_out) {
   __shared__ uint32_t wc[RS_WARPS][256];
+  __shared__ uint32_t dstart[256];  // first tile position of each digit
+  __shared__ uint32_t sw[32];
+  __shared__ uint32_t ks[RS_TILE], vs[RS_TILE];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < RS_WARPS * 256; i += 256) (&wc[0][0])[i] = 0;
   __syncthreads();
-  const size_t sub = (size_t)blockIdx.x * RS_TILE + (size_t)w * RS_SUB;
+  const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
+  const size_t sub = tile0 + (size_t)w * RS_SUB;
   uint32_t k[RS_BATCH], v[RS_BATCH];
 #pragma unroll
   for (int b = 0; b < RS_BATCH; ++b) {
@@ -180,8 +188,12 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const uint32_t* __restrict__
   }
   __syncthreads();
   {
+    // tile position of digit d's first item from warp ww: digits in order, then warps
     const int d = threadIdx.x;
-    uint32_t run = offsets[(size_t)d * tiles + blockIdx.x];
+    uint32_t tot = 0;
+    for (int ww = 0; ww < RS_WARPS; ++ww) tot += wc[ww][d];
+    uint32_t run = block_exclusive_sum<uint32_t>(tot, sw, nullptr);
+    dstart[d] = run;
     for (int ww = 0; ww < RS_WARPS; ++ww) {
       uint32_t c = wc[ww][d];
       wc[ww][d] = run;
@@ -201,11 +213,20 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const uint32_t* __restrict__
     __syncwarp();
     if (ok) {
       uint32_t pos = base + __popc(same & lt);
-      keys_out[pos] = k[b];
-      vals_out[pos] = v[b];
+      ks[pos] = k[b];
+      vs[pos] = v[b];
       if (lane == __ffs(same) - 1) wc[w][d] = base + __popc(same);
     }
     __syncwarp();
+  }
+  __syncthreads();
+  const uint32_t items = (uint32_t)min((size_t)RS_TILE, n - tile0);
+  for (uint32_t i = threadIdx.x; i < items; i += 256) {
+    const uint32_t key = ks[i];
+    const uint32_t d = (key >> shift) & 255u;
+    const uint32_t pos = offsets[(size_t)d * tiles + blockIdx.x] + (i - dstart[d]);
+    keys_out[pos] = key;
+    vals_out[pos] = vs[i];
   }
 }
 
