@@ -517,6 +517,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served workloads")
+    ap.add_argument("--no-probe", action="store_true", help="skip the gather-ceiling probe after the timing")
     ap.add_argument("--ref-attempts", type=int, default=40_000)
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serve", "sweep", "probe"])
     ap.add_argument("--sweep-scales", default="13,17,20,23,27")
@@ -663,6 +664,14 @@ def main():
         line["gpu_over_oracle"] = {"one_core": value / cpu["single_core"]["value"], "all_cores": value / cpu["value"],
                                    "cores": cpu["cores"]}
     roofline["attempts_per_s"] = prof["sampler_attempts"] / (prof["sampler_ms"] / 1e3) if prof["sampler_ms"] else 0.0
+    if not args.no_probe:  # the random-access ceiling the draws run into, measured after the timed region
+        try:
+            best = max(hs.hsaw_probe_gather(32 << 30, 1, 2048, b)[0] for b in (1, 2, 6))
+            roofline["gather_ceiling"] = {"reads_per_s": best, "what": "dependent random 32 B reads over a 32 GB "
+                                          "table, best of 1, 2 and 6 blocks of 256 per SM (bench.py --mode probe)",
+                                          "draws_over_ceiling": roofline["steps_per_s"] / best}
+        except Exception as e:  # e.g. no room beside the graph
+            roofline["gather_ceiling"] = {"unavailable": str(e)[:120]}
     if world == 1 and not args.no_extras:
         # the batched and served workloads, on the same GPU once the billion-edge graph is freed
         g.close()
