@@ -1136,46 +1136,32 @@ __global__ void k_cover_count(const int64_t* __restrict__ node_off, const int32_
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(cov, c);
 }
 
-__global__ void k_ids_to_keys(const int64_t* __restrict__ T, int32_t k, uint32_t* __restrict__ keys,
-                              uint32_t* __restrict__ vals) {
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
-    keys[i] = (uint32_t)T[i];
-    vals[i] = (uint32_t)i;
-  }
-}
-
 hsaw_status cover_count(const Stream& st, hsaw_mode mode, int64_t first, int64_t count, const int64_t* T, int32_t k,
                         uint64_t* cov, cudaStream_t s) {
   *cov = 0;
   if (count <= 0 || k <= 0) return HSAW_OK;
   if (first < 0 || first + count > st.count) return fail(HSAW_E_INVALID, "coverage: walk range outside the stream");
+  // T is a host array of k ids: sort it here (k is at most a few thousand) and search it on the device
+  std::vector<uint32_t> sorted(T, T + k);
+  std::sort(sorted.begin(), sorted.end());
   uint32_t* buf = nullptr;
-  HSAW_TRY(dmalloc((void**)&buf, (size_t)4 * k * 4 + 64, s));
-  int64_t* dT = nullptr;
-  hsaw_status stt = dmalloc((void**)&dT, (size_t)k * 8, s);
-  if (stt != HSAW_OK) { dfree(buf, s); return stt; }
-  uint32_t *k1 = buf, *v1 = buf + k, *k2 = buf + 2 * (size_t)k, *v2 = buf + 3 * (size_t)k;
-  unsigned long long* dcov = (unsigned long long*)(buf + 4 * (size_t)k + 2);
-  dcov = (unsigned long long*)(((uintptr_t)dcov + 7) & ~(uintptr_t)7);
-  cudaMemcpyAsync(dT, T, (size_t)k * 8, cudaMemcpyHostToDevice, s);
-  count_launch();
-  k_ids_to_keys<<<grid_for(k, 256, 1024), 256, 0, s>>>(dT, k, k1, v1);
-  bool alt = false;
-  stt = radix_sort_pairs(k1, v1, k2, v2, (size_t)k, 31, s, &alt);
-  if (stt == HSAW_OK) {
-    cudaMemsetAsync(dcov, 0, 8, s);
+  HSAW_TRY(dmalloc((void**)&buf, (size_t)k * 4 + 64, s));
+  unsigned long long* dcov = (unsigned long long*)(((uintptr_t)(buf + k) + 15) & ~(uintptr_t)7);
+  hsaw_status stt = HSAW_OK;
+  unsigned long long h = 0;
+  if (cudaMemcpyAsync(buf, sorted.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(dcov, 0, 8, s) != cudaSuccess) {
+    stt = fail(HSAW_E_DEVICE, "coverage: upload failed");
+  } else {
     count_launch();
     k_cover_count<<<grid_for(count, 256, 8192), 256, 0, s>>>(st.node_off.p, st.nodes.p, st.edges.p,
-                                                             mode == HSAW_EDGE ? 1 : 0, first, count,
-                                                             alt ? k2 : k1, k, dcov);
-    unsigned long long h = 0;
+                                                             mode == HSAW_EDGE ? 1 : 0, first, count, buf, k, dcov);
     cudaMemcpyAsync(&h, dcov, 8, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
       stt = fail(HSAW_E_DEVICE, "coverage kernel failed");
-    *cov = h;
   }
+  *cov = h;
   dfree(buf, s);
-  dfree(dT, s);
   return stt;
 }
 
