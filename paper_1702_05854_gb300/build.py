@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhsaw.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["primitives.cu", "graph.cu", "sample.cu", "cover.cu", "api.cu", "profile.cu", "runtime.cu", "pool.cu"]
+SOURCES = ["primitives.cu", "graph.cu", "sample.cu", "cover.cu", "api.cu", "profile.cu", "runtime.cu", "pool.cu",
+           "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -93,6 +93,56 @@ static thread_local const volatile int* t_cancel = nullptr;
 void set_cancel_flag(const volatile int* flag) { t_cancel = flag; }
 bool cancel_requested() { return t_cancel && *t_cancel; }
 
+// Counting, greedy and the result of a fixed-N solve over the first q->n_hsaw hits of st.
+static hsaw_status fixed_tail(const Graph& g, const hsaw_query* q, Stream& st, Cover& cv, const uint8_t* cand,
+                              hsaw_result* r, cudaStream_t s) {
+  const int64_t M = q->mode == HSAW_EDGE ? g.m : g.n;
+  const int32_t k = q->k;
+  void* ph = phase_begin(s);
+  HSAW_TRY(cover_build(st, q->mode, 0, q->n_hsaw, cv, s));
+  phase_end(ph, s, PH_COUNT);
+  ph = phase_begin(s);
+  HSAW_TRY(cover_greedy(cv, cand, M, k, r->ids, r->gains, s));
+  phase_end(ph, s, PH_GREEDY);
+  uint64_t last = 0;
+  HSAW_TRY(aid_at(st, q->n_hsaw - 1, &last, s));
+  uint64_t cov = 0;
+  for (int32_t i = 0; i < k; ++i) cov += r->gains[i];
+  const double n = (double)g.n;
+  r->n_selected = k;
+  r->rounds_t = 0;
+  r->cov_Rprime = r->hits_Rprime = r->attempts_Rprime = 0;
+  r->eps_t = NAN;
+  r->hits = (uint64_t)q->n_hsaw;
+  r->attempts = last + 1;
+  r->cov_R = cov;
+  r->spread_base_est = n * (double)r->hits / (double)r->attempts;
+  r->spread_reduction_est = n * (double)cov / (double)r->attempts;
+  r->steps = st.steps;
+  return HSAW_OK;
+}
+
+hsaw_status validate_query(const Graph& g, const hsaw_query* q) {
+  int64_t n_cand = 0;
+  return validate_common(g, q, &n_cand);
+}
+
+hsaw_status solve_fixed_from_stream(const Graph& g, const hsaw_query* q, Stream& st, hsaw_result* r, cudaStream_t s) {
+  if (!q || !r || !r->ids || !r->gains) return fail(HSAW_E_INVALID, "solve: NULL argument");
+  int64_t n_cand = 0;
+  HSAW_TRY(validate_common(g, q, &n_cand));
+  if (q->n_hsaw < 1 || st.count < q->n_hsaw) return fail(HSAW_E_INVALID, "solve: stream shorter than n_hsaw");
+  const int64_t M = q->mode == HSAW_EDGE ? g.m : g.n;
+  Cover cv;
+  uint8_t* cand = nullptr;
+  hsaw_status rc = upload_mask(q->candidate_mask, (size_t)M, false, s, &cand);
+  if (rc == HSAW_OK) rc = fixed_tail(g, q, st, cv, cand, r, s);
+  cudaStreamSynchronize(s);
+  cv.release(s);
+  dfree(cand, s);
+  return rc;
+}
+
 static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cudaStream_t s) {
   if (!q || !r || !r->ids || !r->gains) return fail(HSAW_E_INVALID, "solve: NULL argument");
   int64_t n_cand = 0;
@@ -113,21 +163,7 @@ static hsaw_status solve(const Graph& g, const hsaw_query* q, hsaw_result* r, cu
     void* ph = phase_begin(s);
     HSAW_TRY(stream_extend(g, W.qd, W.st, q->n_hsaw, s));
     phase_end(ph, s, PH_SAMPLE);
-    ph = phase_begin(s);
-    HSAW_TRY(cover_build(W.st, q->mode, 0, q->n_hsaw, W.cv, s));
-    phase_end(ph, s, PH_COUNT);
-    ph = phase_begin(s);
-    HSAW_TRY(cover_greedy(W.cv, W.cand, M, k, r->ids, r->gains, s));
-    phase_end(ph, s, PH_GREEDY);
-    uint64_t last = 0;
-    HSAW_TRY(aid_at(W.st, q->n_hsaw - 1, &last, s));
-    uint64_t cov = 0;
-    for (int32_t i = 0; i < k; ++i) cov += r->gains[i];
-    r->hits = (uint64_t)q->n_hsaw;
-    r->attempts = last + 1;
-    r->cov_R = cov;
-    r->spread_base_est = n * (double)r->hits / (double)r->attempts;
-    r->spread_reduction_est = n * (double)cov / (double)r->attempts;
+    HSAW_TRY(fixed_tail(g, q, W.st, W.cv, W.cand, r, s));
   } else if (q->sampling == HSAW_STOP_RULE) {
     if (!(q->eps > 0.0 && q->eps < 1.0)) return fail(HSAW_E_INVALID, "query: need 0 < eps < 1");
     const double delta = q->delta > 0 ? q->delta : 1.0 / n;

@@ -24,6 +24,19 @@ namespace hsaw {
 static int default_workers(int32_t w) { return w > 0 ? (int)w : 8; }
 
 // ------------------------------------------------------------------ batch
+// Fixed-N instances (that no walk pool serves) are sampled together: multi-instance sampler
+// launches (batch.cu) extend all their streams at once; then worker threads, each on its
+// own stream, run every instance's counting and greedy, and solve the other instances
+// (stopping rule, pooled) whole.  HSAW_BATCH=threads solves every instance on the workers.
+static bool batchable(const hsaw_graph g, const hsaw_query& q) {
+  if (!g || q.sampling != HSAW_FIXED_N || q.n_hsaw < 1 || q.n_sources < 1 || !q.sources) return false;
+  const Graph& G = g->g;
+  if (G.pool.ent && G.pool.seed == q.seed) return false;
+  const bool ok = validate_query(G, &q) == HSAW_OK;  // an invalid one fails on its own path
+  if (!ok) set_error("");
+  return ok;
+}
+
 static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_result* rs, hsaw_status* statuses,
                              int32_t count, int32_t concurrency, cudaStream_t caller) {
   HSAW_CK(cudaStreamSynchronize(caller));
@@ -32,6 +45,59 @@ static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_re
   const int nw = std::max(1, std::min<int>(default_workers(concurrency), count));
   std::vector<hsaw_status> st(count, HSAW_OK);
   std::vector<std::string> msg(count);
+  // the instances sampled together, with their device suspects and streams
+  const char* mode = getenv("HSAW_BATCH");
+  const bool together = !(mode && mode[0] == 't');
+  std::vector<int32_t> joint;
+  std::vector<char> is_joint(count, 0);
+  std::vector<QueryDev> qds;
+  std::vector<Stream> sts;
+  cudaStream_t s0 = nullptr;
+  if (together) {
+    for (int32_t i = 0; i < count; ++i)
+      if (batchable(gs[i], qs[i])) joint.push_back(i);
+    if (!joint.empty()) HSAW_CK(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
+    qds.resize(joint.size());
+    sts.resize(joint.size());
+    std::vector<const Graph*> gp;
+    std::vector<const QueryDev*> qp;
+    std::vector<Stream*> sp;
+    std::vector<int64_t> want;
+    std::vector<int32_t> gi;  // instance of each joint entry
+    for (size_t j = 0; j < joint.size(); ++j) {
+      const int32_t i = joint[j];
+      is_joint[i] = 1;
+      hsaw_status r = query_upload(gs[i]->g, &qs[i], qds[j], s0);
+      if (r == HSAW_OK) r = stream_init(sts[j], 0, qs[i].max_attempts, s0);
+      if (r != HSAW_OK) {
+        st[i] = r;
+        msg[i] = hsaw_last_error();
+        continue;
+      }
+      gp.push_back(&gs[i]->g);
+      qp.push_back(&qds[j]);
+      sp.push_back(&sts[j]);
+      want.push_back(qs[i].n_hsaw);
+      gi.push_back(i);
+    }
+    std::vector<hsaw_status> js(gp.size(), HSAW_OK);
+    const hsaw_status r = gp.empty() ? HSAW_OK
+                                     : batch_sample(gp.data(), qp.data(), sp.data(), want.data(), (int32_t)gp.size(),
+                                                    js.data(), s0);
+    const std::string m = r != HSAW_OK ? std::string(hsaw_last_error()) : std::string();
+    for (size_t t = 0; t < gi.size(); ++t) {
+      if (r != HSAW_OK) {  // the joint launches failed: every instance in them
+        st[gi[t]] = r;
+        msg[gi[t]] = m;
+      } else if (js[t] != HSAW_OK) {
+        st[gi[t]] = js[t];
+        msg[gi[t]] = "batch: attempt budget exhausted before enough hits";
+      }
+    }
+    if (s0) cudaStreamSynchronize(s0);
+  }
+  std::vector<int32_t> pos_of(count, -1);
+  for (size_t j = 0; j < joint.size(); ++j) pos_of[joint[j]] = (int32_t)j;
   std::atomic<int32_t> next{0};
   auto work = [&]() {
     cudaSetDevice(dev);
@@ -40,12 +106,14 @@ static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_re
     for (;;) {
       const int32_t i = next.fetch_add(1);
       if (i >= count) break;
-      if (!gs[i]) {
+      if (is_joint[i]) {
+        if (st[i] == HSAW_OK) st[i] = solve_fixed_from_stream(gs[i]->g, &qs[i], sts[pos_of[i]], &rs[i], s);
+      } else if (!gs[i]) {
         st[i] = fail(HSAW_E_INVALID, "batch: NULL graph");
       } else {
         st[i] = solve_one(gs[i]->g, &qs[i], &rs[i], s);
       }
-      if (st[i] != HSAW_OK) msg[i] = hsaw_last_error();
+      if (st[i] != HSAW_OK && msg[i].empty()) msg[i] = hsaw_last_error();
     }
     if (s) {
       cudaStreamSynchronize(s);
@@ -55,6 +123,14 @@ static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_re
   std::vector<std::thread> th;
   for (int t = 0; t < nw; ++t) th.emplace_back(work);
   for (auto& t : th) t.join();
+  for (size_t j = 0; j < joint.size(); ++j) {
+    query_release(qds[j], s0);
+    sts[j].release(s0);
+  }
+  if (s0) {
+    cudaStreamSynchronize(s0);
+    cudaStreamDestroy(s0);
+  }
   hsaw_status first = HSAW_OK;
   for (int32_t i = 0; i < count; ++i) {
     if (statuses) statuses[i] = st[i];

@@ -509,7 +509,6 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
   st.elem_range[0] = g.n;
   st.elem_range[1] = g.m;
   const uint32_t CHUNK = 256;
-  const uint32_t k0 = (uint32_t)qd.seed, k1 = (uint32_t)(qd.seed >> 32);
   // the walk pool serves this query's attempts below pool.attempts when the walk seed
   // matches and the graph is not a residual one
   const bool pool_ok = g.pool.ent && g.pool.seed == qd.seed && qd.s_list && !qd.edge_removed && !qd.node_removed;
@@ -541,34 +540,39 @@ hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_
       batch = (batch + CHUNK - 1) / CHUNK * CHUNK;
       HSAW_TRY(sample_window(g, qd, st, batch, &new_hits, s));
     }
-    if (new_hits) {
-      // walk offsets, then the hits' nodes and edges re-drawn from their attempt ids
-      HSAW_TRY(st.node_off.ensure((size_t)st.count + new_hits + 1, s, true));
-      HSAW_TRY(st.tmp64.ensure((size_t)new_hits + 1, s));
-      count_launch();
-      k_len_to_u64<<<grid_for(new_hits, 256, 4096), 256, 0, s>>>(st.len.p + st.count, new_hits, st.tmp64.p);
-      HSAW_CK(cudaGetLastError());
-      HSAW_TRY(exclusive_scan_u64(st.tmp64.p, new_hits, st.tmp64.p + new_hits, s));
-      count_launch();
-      k_offsets<<<grid_for((size_t)new_hits + 1, 256, 4096), 256, 0, s>>>(
-          st.tmp64.p, new_hits, st.total_nodes, st.node_off.p + st.count, st.tmp64.p + new_hits);
-      HSAW_CK(cudaGetLastError());
-      uint64_t added = 0;
-      HSAW_CK(cudaMemcpyAsync(&added, st.tmp64.p + new_hits, 8, cudaMemcpyDeviceToHost, s));
-      HSAW_CK(cudaStreamSynchronize(s));
-      const int64_t tot = st.total_nodes + (int64_t)added;
-      HSAW_TRY(st.nodes.ensure((size_t)tot, s, true));
-      HSAW_TRY(st.edges.ensure((size_t)tot, s, true));
-      count_launch();
-      k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, k0, k1, st.aid.p,
-                                                                   st.len.p, st.node_off.p, st.count,
-                                                                   st.count + new_hits, st.nodes.p, st.edges.p);
-      HSAW_CK(cudaGetLastError());
-      st.total_nodes = tot;
-      st.count += new_hits;
-    }
+    HSAW_TRY(stream_take_hits(g, qd, st, new_hits, s));
     st.next_attempt += batch;
   }
+  return HSAW_OK;
+}
+
+hsaw_status stream_take_hits(const Graph& g, const QueryDev& qd, Stream& st, uint32_t new_hits, cudaStream_t s) {
+  if (!new_hits) return HSAW_OK;
+  const uint32_t k0 = (uint32_t)qd.seed, k1 = (uint32_t)(qd.seed >> 32);
+  // walk offsets, then the hits' nodes and edges re-drawn from their attempt ids
+  HSAW_TRY(st.node_off.ensure((size_t)st.count + new_hits + 1, s, true));
+  HSAW_TRY(st.tmp64.ensure((size_t)new_hits + 1, s));
+  count_launch();
+  k_len_to_u64<<<grid_for(new_hits, 256, 4096), 256, 0, s>>>(st.len.p + st.count, new_hits, st.tmp64.p);
+  HSAW_CK(cudaGetLastError());
+  HSAW_TRY(exclusive_scan_u64(st.tmp64.p, new_hits, st.tmp64.p + new_hits, s));
+  count_launch();
+  k_offsets<<<grid_for((size_t)new_hits + 1, 256, 4096), 256, 0, s>>>(
+      st.tmp64.p, new_hits, st.total_nodes, st.node_off.p + st.count, st.tmp64.p + new_hits);
+  HSAW_CK(cudaGetLastError());
+  uint64_t added = 0;
+  HSAW_CK(cudaMemcpyAsync(&added, st.tmp64.p + new_hits, 8, cudaMemcpyDeviceToHost, s));
+  HSAW_CK(cudaStreamSynchronize(s));
+  const int64_t tot = st.total_nodes + (int64_t)added;
+  HSAW_TRY(st.nodes.ensure((size_t)tot, s, true));
+  HSAW_TRY(st.edges.ensure((size_t)tot, s, true));
+  count_launch();
+  k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, k0, k1, st.aid.p, st.len.p,
+                                                               st.node_off.p, st.count, st.count + new_hits,
+                                                               st.nodes.p, st.edges.p);
+  HSAW_CK(cudaGetLastError());
+  st.total_nodes = tot;
+  st.count += new_hits;
   return HSAW_OK;
 }
 

@@ -49,6 +49,9 @@ struct Stream {
 hsaw_status stream_init(Stream& st, uint64_t first_attempt, uint64_t max_attempts, cudaStream_t s);
 // Extend the stream until it holds at least want hits (Alg. 3 loop).
 hsaw_status stream_extend(const Graph& g, const QueryDev& qd, Stream& st, int64_t want, cudaStream_t s);
+// Adopt new_hits hits whose attempt ids and lengths are already at aid/len[st.count ..]:
+// their walk offsets, nodes and edges (re-drawn from the attempt ids), and the count.
+hsaw_status stream_take_hits(const Graph& g, const QueryDev& qd, Stream& st, uint32_t new_hits, cudaStream_t s);
 hsaw_status classify_attempts(const Graph& g, const QueryDev& qd, uint64_t first, int64_t count, int8_t* outcome,
                               int32_t* length, cudaStream_t s);
 
@@ -93,6 +96,17 @@ bool cancel_requested();
 
 // One full solve on `s` (the body of hsaw_solve).
 hsaw_status solve_one(const Graph& g, const hsaw_query* q, hsaw_result* r, cudaStream_t s);
+// The fixed-N solve from a stream that already holds at least q->n_hsaw hits: counting,
+// greedy (Alg. 4 / 7) and the result fields.
+hsaw_status solve_fixed_from_stream(const Graph& g, const hsaw_query* q, Stream& st, hsaw_result* r, cudaStream_t s);
+// Batched fixed-N sampling (batch.cu): extends every stream i to want[i] hits with
+// multi-instance sampler launches.
+// status[i] (in: HSAW_OK to take part) becomes HSAW_E_TIMEOUT when instance i's attempt
+// budget runs out first; the return value reports failures of the launches themselves.
+hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Stream* const* sts, const int64_t* want,
+                         int32_t count, hsaw_status* status, cudaStream_t s);
+// Query checks shared by every solve: mode, 1 <= k <= |C|.
+hsaw_status validate_query(const Graph& g, const hsaw_query* q);
 
 // Stopping-rule constants (Sec. 5.1) and Check (Alg. 5), host FP64.
 void stop_constants(int64_t M, int32_t k, double eps, double delta, double out6[6]);

@@ -57,14 +57,42 @@ def same(a, b):
         assert r[f] == r2[f], f
 
 
-def test_batch_matches_serial(inst):
+@pytest.mark.parametrize("way", ["joint", "threads"])
+def test_batch_matches_serial(inst, monkeypatch, way):
+    """joint: the fixed-N instances sampled together by multi-instance sampler launches;
+    threads: every instance solved whole on the worker threads."""
     graphs, queries = inst
     alone = [hs.hsaw_solve(g, q) for g, q in zip(graphs, queries)]
+    if way == "threads":
+        monkeypatch.setenv("HSAW_BATCH", "threads")
+    else:
+        monkeypatch.delenv("HSAW_BATCH", raising=False)
     for conc in (1, 4, 12):
         out = hs.hsaw_solve_batch(graphs, queries, concurrency=conc)
         for (st, ids, gains, r), a in zip(out, alone):
             assert st == 0
             same((ids, gains, r), a)
+
+
+def test_joint_batch_with_probabilities_and_budgets(inst, monkeypatch):
+    """Probabilistic suspects, a candidate mask, an instance whose attempt budget runs out
+    (HSAW_E_TIMEOUT for it alone) and one with too few candidates (HSAW_E_INVALID)."""
+    monkeypatch.delenv("HSAW_BATCH", raising=False)
+    graphs, queries = inst
+    g0, g1 = graphs[0], graphs[1]
+    q = queries[0]
+    p = synth.probabilities(len(q.sources))
+    M = g1.m
+    cm = (np.arange(M) % 2 == 0).astype(np.uint8)
+    qs = [hs.Query(sources=q.sources, p_fixed=p, mode=hs.HSAW_NODE, k=7, n_hsaw=5000, seed=11),
+          hs.Query(sources=queries[1].sources, mode=hs.HSAW_EDGE, k=9, n_hsaw=7000, seed=12, candidate_mask=cm),
+          hs.Query(sources=q.sources[:1], mode=hs.HSAW_NODE, k=3, n_hsaw=10 ** 6, seed=13, max_attempts=1 << 20),
+          hs.Query(sources=q.sources, mode=hs.HSAW_NODE, k=g0.n + 1, n_hsaw=100, seed=14)]
+    gs = [g0, g1, g0, g0]
+    out = hs.hsaw_solve_batch(gs, qs, concurrency=3)
+    assert [o[0] for o in out] == [0, 0, -7, -1]
+    for (st, ids, gains, r), g, qq in zip(out[:2], gs[:2], qs[:2]):
+        same((ids, gains, r), hs.hsaw_solve(g, qq))
 
 
 def test_batch_reports_per_instance_errors(inst):
