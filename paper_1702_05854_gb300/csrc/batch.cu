@@ -17,8 +17,8 @@
 
 namespace hsaw {
 
-constexpr uint32_t BCHUNK = 256;                       // attempts per chunk (= records per chunk)
-constexpr uint64_t BATCH_ROUND_ATTEMPTS = 1ull << 29;  // attempts of all instances in one launch
+constexpr uint32_t BCHUNK = 256;                       // attempts per chunk
+constexpr uint64_t BATCH_ROUND_ATTEMPTS = 1ull << 32;  // attempts of all instances in one launch
 
 struct BatchInst {
   const uint4* node;
@@ -31,7 +31,8 @@ struct BatchInst {
   uint32_t n_attempts;  // window size
   uint32_t n_chunks;
   uint32_t chunk0;      // first global chunk of the window
-  uint32_t pad;
+  uint32_t cap;         // hit records per chunk (a few standard deviations above the expected hits)
+  uint64_t rec0;        // first record of the window
 };
 
 struct BatchParams {
@@ -39,8 +40,9 @@ struct BatchParams {
   uint32_t K;
   uint32_t* inst_ctr;      // K chunk counters
   uint32_t* chunk_hits;    // all chunks
-  uint2* recs;             // all chunks x BCHUNK
+  uint2* recs;             // the windows' records
   unsigned long long* steps;  // K
+  uint32_t* overflow;      // K: a chunk of the window had more hits than its records
   uint32_t* status;
 };
 
@@ -138,9 +140,10 @@ __global__ void __launch_bounds__(256, 4) k_sample_batch(BatchParams B) {
         if (outcome >= 0) {
           active = false;
           if (outcome == 1) {
-            const uint32_t gc = I.chunk0 + off / BCHUNK;
-            const uint32_t slot = atomicAdd(&B.chunk_hits[gc], 1u);  // < BCHUNK: one record per attempt at most
-            B.recs[(size_t)gc * BCHUNK + slot] = make_uint2(off, len);
+            const uint32_t lc = off / BCHUNK;
+            const uint32_t slot = atomicAdd(&B.chunk_hits[I.chunk0 + lc], 1u);
+            if (slot < I.cap) B.recs[I.rec0 + (size_t)lc * I.cap + slot] = make_uint2(off, len);
+            else B.overflow[i] = 1u;
           }
         }
       }
@@ -151,6 +154,23 @@ __global__ void __launch_bounds__(256, 4) k_sample_batch(BatchParams B) {
   }
 }
 
+// The instance whose window holds chunk gc: the last one with chunk0 <= gc.
+__device__ __forceinline__ uint32_t batch_owner(const BatchInst* __restrict__ inst, uint32_t K, uint32_t gc) {
+  uint32_t lo = 0, hi = K;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (inst[mid].chunk0 <= gc) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Records kept per chunk (its hits, at most its instance's cap), to be scanned.
+__global__ void k_clamp_batch(const BatchInst* __restrict__ inst, uint32_t K, const uint32_t* __restrict__ chunk_hits,
+                              uint32_t n_chunks, uint32_t* __restrict__ kept) {
+  for (uint32_t gc = blockIdx.x * blockDim.x + threadIdx.x; gc < n_chunks; gc += gridDim.x * blockDim.x)
+    kept[gc] = min(chunk_hits[gc], inst[batch_owner(inst, K, gc)].cap);
+}
+
 // Order each chunk's hits by attempt id and write them at the chunk's global offset, as
 // attempt ids of its instance's window.
 __global__ void k_compact_batch(const BatchInst* __restrict__ inst, uint32_t K, const uint32_t* __restrict__ chunk_hits,
@@ -159,15 +179,12 @@ __global__ void k_compact_batch(const BatchInst* __restrict__ inst, uint32_t K, 
   const int lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t gc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gc < n_chunks; gc += warps) {
-    const uint32_t c = chunk_hits[gc];
-    if (c == 0) continue;
-    uint32_t lo = 0, hi = K;  // the instance whose window holds chunk gc: last chunk0 <= gc
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (inst[mid].chunk0 <= gc) lo = mid; else hi = mid;
-    }
-    const uint64_t a0 = inst[lo].a0;
-    const uint2* r = recs + (size_t)gc * BCHUNK;
+    if (chunk_hits[gc] == 0) continue;
+    const uint32_t lo = batch_owner(inst, K, gc);
+    const BatchInst& I = inst[lo];
+    const uint32_t c = min(chunk_hits[gc], I.cap);
+    const uint64_t a0 = I.a0;
+    const uint2* r = recs + I.rec0 + (size_t)(gc - I.chunk0) * I.cap;
     const uint32_t base = chunk_off[gc];
     for (uint32_t q = lane; q < c; q += 32) {
       const uint2 me = r[q];
@@ -191,13 +208,14 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
   std::vector<BatchInst> inst;
   std::vector<int32_t> who;  // instance index of each descriptor
   DBuf<BatchInst> d_inst;
-  DBuf<uint32_t> ctr, chunk_hits, chunk_off, bound;
+  DBuf<uint32_t> ctr, chunk_hits, chunk_off, bound, ovf;
+  std::vector<char> full_cap(count, 0);  // a window overflowed its records: redo it with room for every hit
   DBuf<uint2> recs;
   DBuf<unsigned long long> steps;
   DBuf<uint64_t> out_aid;
   DBuf<uint32_t> out_len;
   auto release = [&]() {
-    d_inst.release(s); ctr.release(s); chunk_hits.release(s); chunk_off.release(s); bound.release(s);
+    d_inst.release(s); ctr.release(s); chunk_hits.release(s); chunk_off.release(s); bound.release(s); ovf.release(s);
     recs.release(s); steps.release(s); out_aid.release(s); out_len.release(s);
   };
   hsaw_status rc = HSAW_OK;
@@ -223,6 +241,7 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
     // windows as the one-instance sampler sizes them, within a per-launch budget
     const double share = std::max(1048576.0, (double)BATCH_ROUND_ATTEMPTS / active);
     uint32_t chunks = 0;
+    uint64_t nrecs = 0;
     for (int32_t i = 0; i < count; ++i) {
       Stream& st = *sts[i];
       if (status[i] != HSAW_OK || st.count >= want[i]) continue;
@@ -250,6 +269,12 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
       b.n_attempts = (uint32_t)batch;
       b.n_chunks = (uint32_t)(batch / BCHUNK);
       b.chunk0 = chunks;
+      const double exp_hits = st.hit_rate * BCHUNK;
+      b.cap = (st.hit_rate == 0.0 || full_cap[i])
+                  ? BCHUNK
+                  : (uint32_t)std::min<double>(BCHUNK, std::ceil(exp_hits + 6.0 * std::sqrt(exp_hits + 1.0) + 8.0));
+      b.rec0 = nrecs;
+      nrecs += (uint64_t)b.n_chunks * b.cap;
       chunks += b.n_chunks;
       inst.push_back(b);
       who.push_back(i);
@@ -257,13 +282,14 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
     const uint32_t K = (uint32_t)inst.size();
     if ((rc = d_inst.ensure(K, s)) != HSAW_OK || (rc = ctr.ensure((size_t)K + 2, s)) != HSAW_OK ||
         (rc = chunk_hits.ensure(chunks, s)) != HSAW_OK || (rc = chunk_off.ensure((size_t)chunks + 1, s)) != HSAW_OK ||
-        (rc = bound.ensure((size_t)K + 1, s)) != HSAW_OK || (rc = recs.ensure((size_t)chunks * BCHUNK, s)) != HSAW_OK ||
-        (rc = steps.ensure(K, s)) != HSAW_OK)
+        (rc = bound.ensure((size_t)K + 1, s)) != HSAW_OK || (rc = recs.ensure((size_t)nrecs, s)) != HSAW_OK ||
+        (rc = steps.ensure(K, s)) != HSAW_OK || (rc = ovf.ensure(K, s)) != HSAW_OK)
       break;
     if (cudaMemcpyAsync(d_inst.p, inst.data(), K * sizeof(BatchInst), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(ctr.p, 0, ((size_t)K + 2) * 4, s) != cudaSuccess ||
         cudaMemsetAsync(chunk_hits.p, 0, (size_t)chunks * 4, s) != cudaSuccess ||
-        cudaMemsetAsync(steps.p, 0, (size_t)K * 8, s) != cudaSuccess) {
+        cudaMemsetAsync(steps.p, 0, (size_t)K * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(ovf.p, 0, (size_t)K * 4, s) != cudaSuccess) {
       rc = fail(HSAW_E_DEVICE, "batch: set-up copies failed");
       break;
     }
@@ -274,6 +300,7 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
     P.chunk_hits = chunk_hits.p;
     P.recs = recs.p;
     P.steps = steps.p;
+    P.overflow = ovf.p;
     P.status = ctr.p + K;
     uint64_t round_attempts = 0;
     for (const BatchInst& b : inst) round_attempts += b.n_attempts;
@@ -282,19 +309,19 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
     k_sample_batch<<<grid, 256, 0, s>>>(P);
     profile_end(prof, s, round_attempts);
     if (cudaGetLastError() != cudaSuccess) { rc = fail(HSAW_E_DEVICE, "batch: sampler launch failed"); break; }
-    if (cudaMemcpyAsync(chunk_off.p, chunk_hits.p, (size_t)chunks * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-      rc = fail(HSAW_E_DEVICE, "batch: copy failed");
-      break;
-    }
+    count_launch();
+    k_clamp_batch<<<grid_for(chunks, 256, 8192), 256, 0, s>>>(d_inst.p, K, chunk_hits.p, chunks, chunk_off.p);
+    if (cudaGetLastError() != cudaSuccess) { rc = fail(HSAW_E_DEVICE, "batch: clamp launch failed"); break; }
     if ((rc = exclusive_scan_u32(chunk_off.p, chunks, chunk_off.p + chunks, s)) != HSAW_OK) break;
     count_launch();
     k_batch_bounds<<<grid_for((size_t)K + 1, 256, 64), 256, 0, s>>>(d_inst.p, K, chunk_off.p, chunk_off.p + chunks,
                                                                      bound.p);
-    std::vector<uint32_t> hb((size_t)K + 1);
+    std::vector<uint32_t> hb((size_t)K + 1), hovf(K);
     std::vector<unsigned long long> hsteps(K);
     uint32_t status = 0;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(hb.data(), bound.p, ((size_t)K + 1) * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hovf.data(), ovf.p, (size_t)K * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(hsteps.data(), steps.p, (size_t)K * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&status, ctr.p + K, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -317,6 +344,11 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
       Stream& st = *sts[who[j]];
       const uint32_t h = hb[j + 1] - hb[j];
       st.steps += hsteps[j];
+      if (hovf[j]) {  // rare: this window is drawn again next round with room for every hit
+        full_cap[who[j]] = 1;
+        continue;
+      }
+      full_cap[who[j]] = 0;
       if (h) {
         if ((rc = st.aid.ensure((size_t)st.count + h, s, true)) != HSAW_OK) break;
         if ((rc = st.len.ensure((size_t)st.count + h, s, true)) != HSAW_OK) break;
