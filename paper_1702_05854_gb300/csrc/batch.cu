@@ -4,7 +4,7 @@
 // instance's hits by attempt id, and each instance adopts its hits (walks re-drawn from
 // their attempt ids).  A warp takes chunks of one instance until that instance's window is
 // exhausted and its lanes are idle, then moves to the next instance, so the lanes of a warp
-// always walk the same graph.  The walks, draws and hit records are those of the one-
+// always walk the same graph; all warps take the instances in the same order.  The walks, draws and hit records are those of the one-
 // instance sampler (Alg. 1-3 with node-keyed Philox draws), so every stream, and with it
 // every result, equals the instance solved alone.
 #include <cuda_runtime.h>
@@ -52,9 +52,10 @@ __global__ void __launch_bounds__(256, 4) k_sample_batch(BatchParams B) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  for (uint32_t t = 0; t < B.K; ++t) {
-    const uint32_t i = (gwarp + t) % B.K;
+  // every warp takes the instances in the same order, so the GPU works through one
+  // instance's window at a time (its graph's hot records stay in L2) and moves on as the
+  // window runs out; warps that finish early start the next instance
+  for (uint32_t i = 0; i < B.K; ++i) {
     const BatchInst I = B.inst[i];
     uint32_t cur = 0, cur_end = 0;
     bool more = true, active = false;

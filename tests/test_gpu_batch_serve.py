@@ -63,10 +63,7 @@ def test_batch_matches_serial(inst, monkeypatch, way):
     threads: every instance solved whole on the worker threads."""
     graphs, queries = inst
     alone = [hs.hsaw_solve(g, q) for g, q in zip(graphs, queries)]
-    if way == "threads":
-        monkeypatch.setenv("HSAW_BATCH", "threads")
-    else:
-        monkeypatch.delenv("HSAW_BATCH", raising=False)
+    monkeypatch.setenv("HSAW_BATCH", way)
     for conc in (1, 4, 12):
         out = hs.hsaw_solve_batch(graphs, queries, concurrency=conc)
         for (st, ids, gains, r), a in zip(out, alone):
@@ -77,7 +74,7 @@ def test_batch_matches_serial(inst, monkeypatch, way):
 def test_joint_batch_with_probabilities_and_budgets(inst, monkeypatch):
     """Probabilistic suspects, a candidate mask, an instance whose attempt budget runs out
     (HSAW_E_TIMEOUT for it alone) and one with too few candidates (HSAW_E_INVALID)."""
-    monkeypatch.delenv("HSAW_BATCH", raising=False)
+    monkeypatch.setenv("HSAW_BATCH", "joint")
     graphs, queries = inst
     g0, g1 = graphs[0], graphs[1]
     q = queries[0]
