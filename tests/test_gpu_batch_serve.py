@@ -71,10 +71,11 @@ def test_batch_matches_serial(inst, monkeypatch, way):
             same((ids, gains, r), a)
 
 
-def test_joint_batch_with_probabilities_and_budgets(inst, monkeypatch):
+@pytest.mark.parametrize("way", ["joint", "threads"])
+def test_batch_with_probabilities_and_budgets(inst, monkeypatch, way):
     """Probabilistic suspects, a candidate mask, an instance whose attempt budget runs out
     (HSAW_E_TIMEOUT for it alone) and one with too few candidates (HSAW_E_INVALID)."""
-    monkeypatch.setenv("HSAW_BATCH", "joint")
+    monkeypatch.setenv("HSAW_BATCH", way)
     graphs, queries = inst
     g0, g1 = graphs[0], graphs[1]
     q = queries[0]
