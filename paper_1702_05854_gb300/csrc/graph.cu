@@ -121,64 +121,39 @@ __global__ void k_copy_edges(const int32_t* __restrict__ src, const uint32_t* __
   }
 }
 
-// Running in-weight sums (exact, 64-bit carry), the in-sum check (<= 2^32 - 1), equal-
-// weight detection and the node record.  A warp takes 32 consecutive nodes: each lane sums
-// its own node's in-list when it has at most 32 in-edges (most nodes of a power-law
-// graph), and the warp then scans the longer lists together, 32 edges at a time.
-__device__ __forceinline__ void store_node(uint4* node, int64_t v, uint32_t b, uint32_t deg, uint64_t carry,
-                                           bool uniform, uint32_t w0) {
-  const uint32_t insum = (uint32_t)(carry > 0xFFFFFFFFull ? 0xFFFFFFFFull : carry);
-  node[v] = make_uint4(b, deg, (uniform && deg) ? w0 : 0u, insum);
-}
-
+// One warp per node: running in-weight sums (exact, 64-bit carry), the in-sum check
+// (<= 2^32 - 1), equal-weight detection and the node record.
 __global__ void k_thresholds(const uint32_t* __restrict__ row_start, int64_t n, uint2* __restrict__ edge,
                              uint4* __restrict__ node, uint32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; v0 < n; v0 += warps * 32) {
-    const int64_t v = v0 + lane;
-    const bool in = v < n;
-    const uint32_t b = in ? row_start[v] : 0u, deg = in ? row_start[v + 1] - b : 0u;
-    if (in && deg <= 32) {  // this lane's own list
-      uint64_t carry = 0;
-      const uint32_t w0 = deg ? edge[b].y : 0u;
-      bool uniform = true;
-      for (uint32_t q = b; q < b + deg; ++q) {
-        const uint32_t w = edge[q].y;
-        uniform &= (w == w0);
-        carry += w;
-        if (carry > 0xFFFFFFFFull) atomicOr(err, ERR_WEIGHT);
-        edge[q].y = (uint32_t)(carry > 0xFFFFFFFFull ? 0xFFFFFFFFull : carry);
-      }
-      store_node(node, v, b, deg, carry, uniform, w0);
-    }
-    unsigned big = __ballot_sync(0xffffffffu, in && deg > 32);
-    while (big) {  // the warp scans each long list
-      const int l = __ffs(big) - 1;
-      big &= big - 1;
-      const uint32_t bb = __shfl_sync(0xffffffffu, b, l), e = bb + __shfl_sync(0xffffffffu, deg, l);
-      uint64_t carry = 0;
-      const uint32_t w0 = edge[bb].y;
-      bool uniform = true;
-      for (uint32_t base = bb; base < e; base += 32) {
-        const uint32_t q = base + lane;
-        const uint64_t w = q < e ? edge[q].y : 0u;
-        if (q < e && (uint32_t)w != w0) uniform = false;
-        uint64_t x = w;
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const uint32_t b = row_start[v], e = row_start[v + 1];
+    const uint32_t deg = e - b;
+    uint64_t carry = 0;
+    uint32_t w0 = deg ? edge[b].y : 0u;
+    bool uniform = true;
+    for (uint32_t base = b; base < e; base += 32) {
+      uint32_t q = base + lane;
+      uint64_t w = q < e ? edge[q].y : 0u;
+      if (q < e && (uint32_t)w != w0) uniform = false;
+      uint64_t x = w;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
-        }
-        const uint64_t run = carry + x;
-        if (q < e) {
-          if (run > 0xFFFFFFFFull) atomicOr(err, ERR_WEIGHT);
-          edge[q].y = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
-        }
-        carry += __shfl_sync(0xffffffffu, x, 31);
+      for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      uniform = __all_sync(0xffffffffu, uniform);
-      if (lane == 0) store_node(node, v0 + l, bb, e - bb, carry, uniform, w0);
+      uint64_t run = carry + x;
+      if (q < e) {
+        if (run > 0xFFFFFFFFull) atomicOr(err, ERR_WEIGHT);
+        edge[q].y = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
+      }
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    uniform = __all_sync(0xffffffffu, uniform);
+    if (lane == 0) {
+      uint32_t insum = (uint32_t)(carry > 0xFFFFFFFFull ? 0xFFFFFFFFull : carry);
+      node[v] = make_uint4(b, deg, (uniform && deg) ? w0 : 0u, insum);
     }
   }
 }
@@ -313,7 +288,7 @@ struct Temps {
 static hsaw_status finish_graph(Graph& g, uint32_t* row_start, uint32_t* d_err, cudaStream_t s) {
   const int64_t n = g.n;
   count_launch();
-  k_thresholds<<<grid_for((size_t)n, 256, 1u << 20), 256, 0, s>>>(row_start, n, g.edge, g.node, d_err);
+  k_thresholds<<<grid_for((size_t)n * 32, 256, 1u << 20), 256, 0, s>>>(row_start, n, g.edge, g.node, d_err);
   HSAW_CK(cudaGetLastError());
   HSAW_TRY(check_err(d_err, s));
   if (g.m) {
