@@ -1,8 +1,8 @@
 // Multi-instance sampling for batches of fixed-N solves: one persistent sampler launch per
 // round serves a window of attempts of every instance that still needs hits (each with its
 // own graph, suspects and walk seed), then one scan and one compaction order every
-// instance's hits by attempt id, and each instance adopts its hits (walks re-drawn from
-// their attempt ids).  A warp takes chunks of one instance until that instance's window is
+// instance's hits by attempt id and append them to its stream as attempt ids and lengths;
+// the caller then draws each instance's walks from their attempt ids (in parallel).  A warp takes chunks of one instance until that instance's window is
 // exhausted and its lanes are idle, then moves to the next instance, so the lanes of a warp
 // always walk the same graph; all warps take the instances in the same order.  The walks, draws and hit records are those of the one-
 // instance sampler (Alg. 1-3 with node-keyed Philox draws), so every stream, and with it
@@ -205,7 +205,7 @@ __global__ void k_batch_bounds(const BatchInst* __restrict__ inst, uint32_t K, c
 }
 
 hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Stream* const* sts, const int64_t* want,
-                         int32_t count, hsaw_status* status, cudaStream_t s) {
+                         int32_t count, hsaw_status* status, int64_t* staged, cudaStream_t s) {
   std::vector<BatchInst> inst;
   std::vector<int32_t> who;  // instance index of each descriptor
   DBuf<BatchInst> d_inst;
@@ -223,6 +223,7 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
   for (int32_t i = 0; i < count; ++i) {
     sts[i]->elem_range[0] = gs[i]->n;
     sts[i]->elem_range[1] = gs[i]->m;
+    staged[i] = 0;
   }
   const int grid = sm_count() * 4;
   for (;;) {
@@ -231,7 +232,7 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
     who.clear();
     int32_t active = 0;
     for (int32_t i = 0; i < count; ++i) {
-      if (status[i] != HSAW_OK || sts[i]->count >= want[i]) continue;
+      if (status[i] != HSAW_OK || sts[i]->count + staged[i] >= want[i]) continue;
       if (sts[i]->next_attempt - sts[i]->first_attempt >= sts[i]->max_attempts) {
         status[i] = HSAW_E_TIMEOUT;  // this instance alone: its attempt budget ran out
         continue;
@@ -245,11 +246,12 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
     uint64_t nrecs = 0;
     for (int32_t i = 0; i < count; ++i) {
       Stream& st = *sts[i];
-      if (status[i] != HSAW_OK || st.count >= want[i]) continue;
+      const int64_t have = st.count + staged[i];
+      if (status[i] != HSAW_OK || have >= want[i]) continue;
       const uint64_t used = st.next_attempt - st.first_attempt;
-      const double need = (double)(want[i] - st.count);
-      st.hit_rate = used ? (double)st.count / (double)used : 0.0;
-      const double margin = std::min(1.25, 1.0 + 4.0 / std::sqrt(std::max(1.0, (double)st.count)) + 4.0 / std::sqrt(need));
+      const double need = (double)(want[i] - have);
+      st.hit_rate = used ? (double)have / (double)used : 0.0;
+      const double margin = std::min(1.25, 1.0 + 4.0 / std::sqrt(std::max(1.0, (double)have)) + 4.0 / std::sqrt(need));
       double target = st.hit_rate > 0 ? need / st.hit_rate * margin + 4096.0 : std::max(1048576.0, 2.0 * (double)used);
       target = std::min(std::max(target, 1048576.0), std::min(share, 268435456.0));
       uint64_t batch = std::min<uint64_t>((uint64_t)target, st.max_attempts - used);
@@ -350,17 +352,16 @@ hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Str
         continue;
       }
       full_cap[who[j]] = 0;
-      if (h) {
-        if ((rc = st.aid.ensure((size_t)st.count + h, s, true)) != HSAW_OK) break;
-        if ((rc = st.len.ensure((size_t)st.count + h, s, true)) != HSAW_OK) break;
-        if (cudaMemcpyAsync(st.aid.p + st.count, out_aid.p + hb[j], (size_t)h * 8, cudaMemcpyDeviceToDevice, s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(st.len.p + st.count, out_len.p + hb[j], (size_t)h * 4, cudaMemcpyDeviceToDevice, s) !=
-                cudaSuccess) {
+      if (h) {  // staged after the stream's adopted hits; their walks are drawn by the caller
+        const size_t at = (size_t)(st.count + staged[who[j]]);
+        if ((rc = st.aid.ensure(at + h, s, true)) != HSAW_OK) break;
+        if ((rc = st.len.ensure(at + h, s, true)) != HSAW_OK) break;
+        if (cudaMemcpyAsync(st.aid.p + at, out_aid.p + hb[j], (size_t)h * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(st.len.p + at, out_len.p + hb[j], (size_t)h * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
           rc = fail(HSAW_E_DEVICE, "batch: hit copy failed");
           break;
         }
-        rc = stream_take_hits(*gs[who[j]], *qds[who[j]], st, h, s);
+        staged[who[j]] += h;
       }
       st.next_attempt += inst[j].n_attempts;
     }

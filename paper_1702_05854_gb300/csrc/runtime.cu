@@ -55,6 +55,8 @@ static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_re
   const bool together = mode && mode[0] == 'j';
   std::vector<int32_t> joint;
   std::vector<char> is_joint(count, 0);
+  std::vector<int64_t> staged;           // per joint entry: sampled hits whose walks are still to draw
+  std::vector<int32_t> pos_in_joint(count, -1);
   std::vector<QueryDev> qds;
   std::vector<Stream> sts;
   cudaStream_t s0 = nullptr;
@@ -64,6 +66,8 @@ static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_re
     if (!joint.empty()) HSAW_CK(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
     qds.resize(joint.size());
     sts.resize(joint.size());
+    staged.assign(joint.size(), 0);
+    for (size_t j = 0; j < joint.size(); ++j) pos_in_joint[joint[j]] = (int32_t)j;
     std::vector<const Graph*> gp;
     std::vector<const QueryDev*> qp;
     std::vector<Stream*> sp;
@@ -86,9 +90,11 @@ static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_re
       gi.push_back(i);
     }
     std::vector<hsaw_status> js(gp.size(), HSAW_OK);
+    std::vector<int64_t> stg(gp.size(), 0);
     const hsaw_status r = gp.empty() ? HSAW_OK
                                      : batch_sample(gp.data(), qp.data(), sp.data(), want.data(), (int32_t)gp.size(),
-                                                    js.data(), s0);
+                                                    js.data(), stg.data(), s0);
+    for (size_t t = 0; t < gi.size(); ++t) staged[pos_in_joint[gi[t]]] = stg[t];
     const std::string m = r != HSAW_OK ? std::string(hsaw_last_error()) : std::string();
     for (size_t t = 0; t < gi.size(); ++t) {
       if (r != HSAW_OK) {  // the joint launches failed: every instance in them
@@ -112,7 +118,9 @@ static hsaw_status run_batch(const hsaw_graph* gs, const hsaw_query* qs, hsaw_re
       const int32_t i = next.fetch_add(1);
       if (i >= count) break;
       if (is_joint[i]) {
-        if (st[i] == HSAW_OK) st[i] = solve_fixed_from_stream(gs[i]->g, &qs[i], sts[pos_of[i]], &rs[i], s);
+        const int32_t j = pos_of[i];
+        if (st[i] == HSAW_OK) st[i] = stream_take_hits(gs[i]->g, qds[j], sts[j], (uint32_t)staged[j], s);
+        if (st[i] == HSAW_OK) st[i] = solve_fixed_from_stream(gs[i]->g, &qs[i], sts[j], &rs[i], s);
       } else if (!gs[i]) {
         st[i] = fail(HSAW_E_INVALID, "batch: NULL graph");
       } else {

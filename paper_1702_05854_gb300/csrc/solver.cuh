@@ -103,8 +103,10 @@ hsaw_status solve_fixed_from_stream(const Graph& g, const hsaw_query* q, Stream&
 // multi-instance sampler launches.
 // status[i] (in: HSAW_OK to take part) becomes HSAW_E_TIMEOUT when instance i's attempt
 // budget runs out first; the return value reports failures of the launches themselves.
+// staged[i] receives the number of hits appended to stream i's aid/len after its count:
+// stream_take_hits(..., staged[i]) draws their walks.
 hsaw_status batch_sample(const Graph* const* gs, const QueryDev* const* qds, Stream* const* sts, const int64_t* want,
-                         int32_t count, hsaw_status* status, cudaStream_t s);
+                         int32_t count, hsaw_status* status, int64_t* staged, cudaStream_t s);
 // Query checks shared by every solve: mode, 1 <= k <= |C|.
 hsaw_status validate_query(const Graph& g, const hsaw_query* q);
 
