@@ -30,9 +30,8 @@ static int default_workers(int32_t w) { return w > 0 ? (int)w : 8; }
 // walk pool serves are sampled together instead: multi-instance sampler launches
 // (batch.cu) extend all their streams at once, then the workers run every instance's
 // counting and greedy.  Both give each instance's result alone; the joint form measured
-// slower on every mix tried (the 256-instance batch 0.92x against 1.02x of serial; 256
-// graphs of at most 10^4 nodes 2.06x against 2.49x), because adopting each instance's hits
-// runs on one host thread while the workers overlap everything.
+// no faster on any mix tried (the 256-instance batch 0.93x against 1.02x of serial; 256
+// graphs of at most 10^4 nodes 2.29x against 2.34-2.49x).
 static bool batchable(const hsaw_graph g, const hsaw_query& q) {
   if (!g || q.sampling != HSAW_FIXED_N || q.n_hsaw < 1 || q.n_sources < 1 || !q.sources) return false;
   const Graph& G = g->g;
