@@ -27,7 +27,7 @@ void Cover::release(cudaStream_t s) {
   keys.release(s); vals.release(s); keys2.release(s); vals2.release(s); run_flag.release(s);
   uid.release(s); cnt.release(s); inv_off.release(s); inv_walk.release(s); entry_uidx.release(s);
   walk_eoff.release(s); cnt_work.release(s); covered.release(s); dirty.release(s); partial.release(s);
-  inv_ent.release(s);
+  inv_ent.release(s); g_idx.release(s); g_list.release(s); g_cnt.release(s); g_entry.release(s); g_rng.release(s);
 }
 
 // entry offsets of walks [first, first + count) relative to the first walk's first entry
@@ -450,14 +450,18 @@ namespace cg = cooperative_groups;
 
 constexpr unsigned long long KEY_UNKNOWN = ~0ull;  // above every element key (counts < 2^31)
 
+// Entries of walk elements that the greedy does not track carry this index.
+constexpr uint32_t UNTRACKED = 0xFFFFFFFFu;
+
 struct ClusterGreedyParams {
   uint32_t U, NG, per_cta, gshift;
   uint32_t short_walks;  // 1: walks average few elements, cover one walk per thread
+  uint32_t min_gain;     // stop before a pick whose gain is below this (>= 1)
   int32_t k;
   uint32_t* cnt;  // running counts | EXCLUDED
-  const uint32_t* inv_off;
+  const uint2* rng;      // per element: its entries [x, y) of inv_ent
   const uint4* inv_ent;  // {walk, first entry, end entry, 0} per inverted-index entry
-  const uint32_t* entry_uidx;
+  const uint32_t* entry_uidx;  // per walk entry: element index, or UNTRACKED
   uint8_t* covered;
   uint32_t* out_u;
   uint32_t* out_gain;
@@ -468,6 +472,7 @@ struct ClusterGreedyParams {
 // owner CTA when x is the element of that group's largest key.
 __device__ __forceinline__ void cover_decrement(const ClusterGreedyParams& P, cg::cluster_group& cluster,
                                                 unsigned long long* gkey, uint32_t* sbits, uint32_t x) {
+  if (x == UNTRACKED) return;
   atomicSub(&P.cnt[x], 1u);
   const uint32_t gg = x >> P.gshift, owner = gg / P.per_cta, gl = gg % P.per_cta;
   const unsigned long long top = *cluster.map_shared_rank(&gkey[gl], owner);
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
     key = lane < (int)C ? slot[lane] : 0ull;
     key = warp_max_u64(key);
     const uint32_t gain = (uint32_t)(key >> 32);
-    if (gain == 0) break;  // every remaining gain is zero: the same decision in every CTA
+    if (gain < P.min_gain) break;  // the same decision in every CTA (gain 0: every remaining gain is zero)
     const uint32_t u = 0xFFFFFFFFu - (uint32_t)key;
     if (rank == 0 && threadIdx.x == 0) {
       P.out_u[r] = u;
@@ -549,7 +554,8 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
     }
     // 3. cover its walks (one thread per walk when walks are short, one warp per walk
     //    otherwise); the group keys read by cover_decrement do not change until step 1
-    const uint32_t q0 = P.inv_off[u], q1 = P.inv_off[u + 1];
+    const uint2 qr = P.rng[u];
+    const uint32_t q0 = qr.x, q1 = qr.y;
     if (P.short_walks) {
       for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
         const uint4 ent = __ldg(&P.inv_ent[q]);
@@ -591,11 +597,12 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams 
 struct OnchipGreedyParams {
   uint32_t U, per;        // elements, elements per CTA
   uint32_t short_walks;
+  uint32_t min_gain;      // stop before a pick whose gain is below this (>= 1)
   int32_t k;
   const uint32_t* cnt0;   // initial counts | EXCLUDED (U)
-  const uint32_t* inv_off;  // U + 1
+  const uint2* rng;       // U: each element's entries [x, y) of inv_ent
   const uint4* inv_ent;
-  const uint32_t* entry_uidx;
+  const uint32_t* entry_uidx;  // per walk entry: element index, or UNTRACKED
   uint8_t* covered;
   uint32_t* out_u;
   uint32_t* out_gain;
@@ -607,6 +614,7 @@ constexpr uint32_t ONCHIP_GROUP = 32;
 __device__ __forceinline__ void onchip_decrement(const OnchipGreedyParams& P, cg::cluster_group& cluster,
                                                  uint32_t* cnt_s, unsigned long long* gkey, uint32_t* sbits,
                                                  uint32_t x) {
+  if (x == UNTRACKED) return;
   const uint32_t owner = x / P.per, lx = x - owner * P.per, gl = lx / ONCHIP_GROUP;
   atomicSub(cluster.map_shared_rank(&cnt_s[lx], owner), 1u);
   const unsigned long long top = *cluster.map_shared_rank(&gkey[gl], owner);
@@ -626,14 +634,14 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_onchip(OnchipGreedyParams P)
   const uint32_t ng = (per + ONCHIP_GROUP - 1) / ONCHIP_GROUP;
   const uint32_t words = (ng + 31) / 32;
   unsigned long long* gkey = smem_u64;                       // ng
-  uint32_t* cnt_s = reinterpret_cast<uint32_t*>(gkey + ng);  // per
-  uint32_t* off_s = cnt_s + per;                             // per + 1
-  uint32_t* sbits = off_s + per + 1;                         // words
+  uint2* rng_s = reinterpret_cast<uint2*>(gkey + ng);        // per
+  uint32_t* cnt_s = reinterpret_cast<uint32_t*>(rng_s + per);  // per
+  uint32_t* sbits = cnt_s + per;                             // words
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t base = rank * per;
   const uint32_t own = P.U > base ? min(per, P.U - base) : 0;
   for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) cnt_s[i] = i < own ? P.cnt0[base + i] : EXCLUDED;
-  for (uint32_t i = threadIdx.x; i <= own; i += blockDim.x) off_s[i] = P.inv_off[base + i];
+  for (uint32_t i = threadIdx.x; i < own; i += blockDim.x) rng_s[i] = P.rng[base + i];
   for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sbits[i] = 0xFFFFFFFFu;
   for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) gkey[i] = 0;
   cluster.sync();
@@ -666,8 +674,8 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_onchip(OnchipGreedyParams P)
       key = warp_max_u64(key);
       unsigned long long rng = 0;
       if (key) {
-        const uint32_t lx = 0xFFFFFFFFu - (uint32_t)key - base;
-        rng = ((unsigned long long)off_s[lx] << 32) | off_s[lx + 1];
+        const uint2 qr = rng_s[0xFFFFFFFFu - (uint32_t)key - base];
+        rng = ((unsigned long long)qr.x << 32) | qr.y;
       }
       if (lane < (int)C) {
         *cluster.map_shared_rank(&slot_key[rank], lane) = key;
@@ -678,7 +686,7 @@ __global__ void __launch_bounds__(1024, 1) k_greedy_onchip(OnchipGreedyParams P)
     key = lane < (int)C ? slot_key[lane] : 0ull;
     const unsigned long long best = warp_max_u64(key);
     const uint32_t gain = (uint32_t)(best >> 32);
-    if (gain == 0) break;  // every remaining gain is zero: the same decision in every CTA
+    if (gain < P.min_gain) break;  // the same decision in every CTA (gain 0: every remaining gain is zero)
     const uint32_t u = 0xFFFFFFFFu - (uint32_t)best;
     const uint32_t winner = u / per;
     const unsigned long long rng = slot_rng[winner];
@@ -835,45 +843,56 @@ static ClusterCfg cluster_cfg_for(Kernel kernel) {
   return c;
 }
 
-// The greedy with on-chip counts when one cluster's shared memory holds every touched
-// element's count and walk-list offsets; *done = false leaves the other versions to run.
-static hsaw_status onchip_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k, uint32_t* outs, uint32_t* ctl,
-                                 uint32_t csize, bool short_walks, int32_t* rounds, bool* done, cudaStream_t s) {
+// The elements a cluster greedy works on: U of them with running counts (| EXCLUDED), each
+// element's entries [x, y) of cv.inv_ent, and per walk entry the element's index (or
+// UNTRACKED).  The caller sets up the counts and clears the covered flags.
+struct GreedyView {
+  uint32_t U = 0;
+  uint32_t* cnt = nullptr;
+  const uint2* rng = nullptr;
+  const uint32_t* eidx = nullptr;
+};
+
+static void log_greedy(const char* kind, const Cover& cv, const GreedyView& V, uint32_t csize, const char* what,
+                       uint32_t size, int32_t k, cudaEvent_t ev0, cudaEvent_t ev1) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  fprintf(stderr, "hsaw: %s walks=%lld entries=%lld unique=%u cluster=%u %s=%u k=%d ms=%.3f\n", kind,
+          (long long)cv.walks, (long long)cv.entries, V.U, csize, what, size, k, ms);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+}
+
+// The greedy with on-chip counts when one cluster's shared memory holds every element's
+// count and walk-list range; *done = false leaves the other versions to run.
+static hsaw_status onchip_greedy(Cover& cv, const GreedyView& V, int32_t k, uint32_t min_gain, uint32_t* out_u,
+                                 uint32_t* out_gain, uint32_t* ctl, uint32_t csize, bool short_walks, int32_t* rounds,
+                                 bool* done, cudaStream_t s) {
   static const ClusterCfg cfg1 = cluster_cfg_for(k_greedy_onchip);
   if (!cfg1.size) return HSAW_OK;
-  const uint32_t U = (uint32_t)cv.unique;
+  const uint32_t U = V.U;
   auto need = [](uint32_t per) {
     const size_t ng = (per + ONCHIP_GROUP - 1) / ONCHIP_GROUP;
-    return ng * 8 + (size_t)per * 4 + ((size_t)per + 1) * 4 + (ng + 31) / 32 * 4 + 64;
+    return ng * 8 + (size_t)per * 8 + (size_t)per * 4 + (ng + 31) / 32 * 4 + 64;
   };
   auto per_for = [U](uint32_t c) { return (uint32_t)(((uint64_t)U + c - 1) / c + 31) / 32 * 32; };
   csize = std::min<uint32_t>(std::max<uint32_t>(csize, 1), (uint32_t)cfg1.size);
   while (need(per_for(csize)) > cfg1.smem_cap && (int)csize < cfg1.size) csize *= 2;
   const uint32_t per = per_for(csize);
   if (need(per) > cfg1.smem_cap) return HSAW_OK;
-  HSAW_TRY(cv.cnt_work.ensure(U, s));
-  HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
-  HSAW_TRY(cv.inv_ent.ensure((size_t)cv.entries, s));
-  HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
-  count_launch();
-  k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);
-  HSAW_CK(cudaGetLastError());
-  count_launch();
-  k_inv_ranges<<<grid_for((size_t)cv.entries, 256, 8192), 256, 0, s>>>(cv.inv_walk.p, cv.walk_eoff.p,
-                                                                      (uint32_t)cv.entries, cv.inv_ent.p);
-  HSAW_CK(cudaGetLastError());
   OnchipGreedyParams P;
   P.U = U;
   P.per = per;
   P.short_walks = short_walks ? 1u : 0u;
+  P.min_gain = min_gain;
   P.k = k;
-  P.cnt0 = cv.cnt_work.p;
-  P.inv_off = cv.inv_off.p;
+  P.cnt0 = V.cnt;
+  P.rng = V.rng;
   P.inv_ent = cv.inv_ent.p;
-  P.entry_uidx = cv.entry_uidx.p;
+  P.entry_uidx = V.eidx;
   P.covered = cv.covered.p;
-  P.out_u = outs;
-  P.out_gain = outs + k;
+  P.out_u = out_u;
+  P.out_gain = out_gain;
   P.ctl = ctl;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -900,24 +919,18 @@ static hsaw_status onchip_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k, 
   HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
   if (log) cudaEventRecord(ev1, s);
   HSAW_CK(cudaStreamSynchronize(s));
-  if (log) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    fprintf(stderr, "hsaw: k_greedy_onchip walks=%lld entries=%lld unique=%u cluster=%u per=%u k=%d ms=%.3f\n",
-            (long long)cv.walks, (long long)cv.entries, U, csize, per, k, ms);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-  }
+  if (log) log_greedy("k_greedy_onchip", cv, V, csize, "per", per, k, ev0, ev1);
   *rounds = (int32_t)h[3];
   *done = true;
   return HSAW_OK;
 }
 
-// Launch the cluster greedy when one cluster's shared memory holds the group maxima;
-// *done = false leaves the grid-wide version to run.  HSAW_GREEDY=grid selects the grid-wide
-// version, HSAW_GREEDY=cluster the cluster version with counts in global memory (tests).
-static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k, uint32_t* outs, uint32_t* ctl,
-                                  int32_t* rounds, bool* done, cudaStream_t s) {
+// The cluster greedies (on-chip counts when they fit, else counts in global memory with the
+// group maxima in shared memory); *done = false when no cluster can run it.  HSAW_GREEDY=grid
+// selects the grid-wide version, HSAW_GREEDY=cluster the version with counts in global memory
+// (tests).
+static hsaw_status cluster_greedy(Cover& cv, const GreedyView& V, int32_t k, uint32_t min_gain, uint32_t* out_u,
+                                  uint32_t* out_gain, uint32_t* ctl, int32_t* rounds, bool* done, cudaStream_t s) {
   *done = false;
   const char* force = getenv("HSAW_GREEDY");
   if (force && force[0] == 'g') return HSAW_OK;
@@ -925,7 +938,7 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   const int cluster_size = cfg0.size;
   const size_t smem_cap = cfg0.smem_cap;
   if (!cluster_size) return HSAW_OK;
-  const uint32_t U = (uint32_t)cv.unique;
+  const uint32_t U = V.U;
   // a cluster whose shared memory holds the keys of 256-element groups; beyond the largest
   // cluster, larger groups
   auto need = [](uint32_t per) { return (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64; };
@@ -937,7 +950,7 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   const bool short_walks = walks > 0 && (uint64_t)cv.entries < 8ull * walks;
   while ((int)csize < cluster_size && ((uint64_t)csize << 14) < (uint64_t)cv.entries) csize *= 2;
   if (!(force && strcmp(force, "cluster") == 0)) {
-    HSAW_TRY(onchip_greedy(cv, cand_dev, k, outs, ctl, csize, short_walks, rounds, done, s));
+    HSAW_TRY(onchip_greedy(cv, V, k, min_gain, out_u, out_gain, ctl, csize, short_walks, rounds, done, s));
     if (*done) return HSAW_OK;
   }
   per = (NG + csize - 1) / csize;
@@ -961,32 +974,21 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
     NG = ng2;
     per = per2;
   }
-  const size_t smem = need(per);
-  HSAW_TRY(cv.cnt_work.ensure(U, s));
-  HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
-  HSAW_TRY(cv.inv_ent.ensure((size_t)cv.entries, s));
-  HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
-  count_launch();
-  k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);
-  HSAW_CK(cudaGetLastError());
-  count_launch();
-  k_inv_ranges<<<grid_for((size_t)cv.entries, 256, 8192), 256, 0, s>>>(cv.inv_walk.p, cv.walk_eoff.p,
-                                                                      (uint32_t)cv.entries, cv.inv_ent.p);
-  HSAW_CK(cudaGetLastError());
   ClusterGreedyParams P;
   P.U = U;
   P.NG = NG;
   P.per_cta = per;
   P.gshift = gshift;
   P.short_walks = short_walks ? 1u : 0u;
+  P.min_gain = min_gain;
   P.k = k;
-  P.cnt = cv.cnt_work.p;
-  P.inv_off = cv.inv_off.p;
+  P.cnt = V.cnt;
+  P.rng = V.rng;
   P.inv_ent = cv.inv_ent.p;
-  P.entry_uidx = cv.entry_uidx.p;
+  P.entry_uidx = V.eidx;
   P.covered = cv.covered.p;
-  P.out_u = outs;
-  P.out_gain = outs + k;
+  P.out_u = out_u;
+  P.out_gain = out_gain;
   P.ctl = ctl;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -996,7 +998,7 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(csize);
   cfg.blockDim = dim3(1024);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = need(per);
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
@@ -1013,17 +1015,71 @@ static hsaw_status cluster_greedy(Cover& cv, const uint8_t* cand_dev, int32_t k,
   HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
   if (log) cudaEventRecord(ev1, s);
   HSAW_CK(cudaStreamSynchronize(s));
-  if (log) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    fprintf(stderr, "hsaw: k_greedy_cluster walks=%lld entries=%lld unique=%u cluster=%u gshift=%u k=%d ms=%.3f\n",
-            (long long)cv.walks, (long long)cv.entries, U, csize, gshift, k, ms);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-  }
+  if (log) log_greedy("k_greedy_cluster", cv, V, csize, "gshift", gshift, k, ev0, ev1);
   *rounds = (int32_t)h[3];
   *done = true;
   return HSAW_OK;
+}
+
+// ------------------------------------------------------------------ heavy elements first
+// An element that occurs in one walk only can gain at most 1, so while some candidate
+// still gains 2 or more the argmax is among the candidates that occurred at least twice
+// (on R-MAT walks most touched edges occur once).  The greedy first runs on those alone,
+// a smaller set whose counts stay in L2 or shared memory, and stops before a pick of gain
+// below 2; the remaining picks then run on every element, with counts recounted over the
+// walks not covered yet.  The picks are those of the greedy on every element.
+__global__ void k_heavy_flags(const int32_t* __restrict__ uid, const uint32_t* __restrict__ cnt, uint32_t U,
+                              const uint8_t* __restrict__ cand, uint32_t* __restrict__ flag) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
+    flag[u] = (cnt[u] >= 2u && (!cand || cand[uid[u]])) ? 1u : 0u;
+}
+
+// hidx = exclusive scan of the flags: heavy element u gets index hidx[u]
+__global__ void k_heavy_view(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ inv_off,
+                             const uint32_t* __restrict__ hidx, uint32_t U, uint32_t* __restrict__ hlist,
+                             uint32_t* __restrict__ cnt_h, uint2* __restrict__ rng_h) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
+    const uint32_t h = hidx[u];
+    if (hidx[u + 1] != h) {
+      hlist[h] = u;
+      cnt_h[h] = cnt[u];
+      rng_h[h] = make_uint2(inv_off[u], inv_off[u + 1]);
+    }
+  }
+}
+
+__global__ void k_heavy_entries(const uint32_t* __restrict__ entry_uidx, const uint32_t* __restrict__ hidx, uint32_t E,
+                                uint32_t* __restrict__ entry_h) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < E; p += gridDim.x * blockDim.x) {
+    const uint32_t u = entry_uidx[p];
+    entry_h[p] = hidx[u + 1] != hidx[u] ? hidx[u] : UNTRACKED;
+  }
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ inv_off, uint32_t U, uint2* __restrict__ rng) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x)
+    rng[u] = make_uint2(inv_off[u], inv_off[u + 1]);
+}
+
+// picks of the heavy phase: heavy index -> unique index
+__global__ void k_map_picks(uint32_t* __restrict__ out_u, int32_t r, const uint32_t* __restrict__ hlist) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x) out_u[i] = hlist[out_u[i]];
+}
+
+// counts over the walks not covered yet (| EXCLUDED for non-candidates and picked elements)
+__global__ void k_recount(const int32_t* __restrict__ uid, const uint32_t* __restrict__ inv_off,
+                          const uint32_t* __restrict__ inv_walk, const uint8_t* __restrict__ covered, uint32_t U,
+                          const uint8_t* __restrict__ cand, uint32_t* __restrict__ cnt_work) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
+    uint32_t c = 0;
+    for (uint32_t q = inv_off[u]; q < inv_off[u + 1]; ++q) c += covered[inv_walk[q]] ? 0u : 1u;
+    cnt_work[u] = c | ((cand && !cand[uid[u]]) ? EXCLUDED : 0u);
+  }
+}
+
+__global__ void k_exclude_picks(const uint32_t* __restrict__ out_u, int32_t r, uint32_t* __restrict__ cnt_work) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x)
+    atomicOr(&cnt_work[out_u[i]], EXCLUDED);
 }
 
 hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t k, int64_t* ids_host,
@@ -1040,11 +1096,100 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
   hsaw_status st = HSAW_OK;
   bool done = false;
   if (U > 0 && cv.walks > 0) {
-    st = cluster_greedy(cv, cand_dev, k, outs.p, ctl, &rounds, &done, s);
-    if (st == HSAW_OK && done && rounds > 0) {
+    HSAW_TRY(cv.cnt_work.ensure(U, s));
+    HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
+    HSAW_TRY(cv.inv_ent.ensure((size_t)cv.entries, s));
+    HSAW_TRY(cv.g_rng.ensure(U, s));
+    HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
+    count_launch();
+    k_inv_ranges<<<grid_for((size_t)cv.entries, 256, 8192), 256, 0, s>>>(cv.inv_walk.p, cv.walk_eoff.p,
+                                                                        (uint32_t)cv.entries, cv.inv_ent.p);
+    HSAW_CK(cudaGetLastError());
+    // the heavy elements first, when they are clearly fewer than all
+    const char* heavy_env = getenv("HSAW_GREEDY_HEAVY");
+    const char* force = getenv("HSAW_GREEDY");
+    bool heavy_done = false;
+    if (!(heavy_env && heavy_env[0] == '0') && !(force && force[0] == 'g') && U >= 4096) {
+      HSAW_TRY(cv.g_idx.ensure((size_t)U + 1, s));
       count_launch();
-      k_pick_ids<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(outs.p, cv.uid.p, rounds, ids.p);
-      if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: id launch failed");
+      k_heavy_flags<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.g_idx.p);
+      HSAW_CK(cudaGetLastError());
+      HSAW_TRY(exclusive_scan_u32(cv.g_idx.p, U, cv.g_idx.p + U, s));
+      uint32_t H = 0;
+      HSAW_CK(cudaMemcpyAsync(&H, cv.g_idx.p + U, 4, cudaMemcpyDeviceToHost, s));
+      HSAW_CK(cudaStreamSynchronize(s));
+      if (H > 0 && (uint64_t)H * 4 <= (uint64_t)U * 3) {
+        HSAW_TRY(cv.g_list.ensure(H, s));
+        HSAW_TRY(cv.g_cnt.ensure(H, s));
+        HSAW_TRY(cv.g_entry.ensure((size_t)cv.entries, s));
+        count_launch();
+        k_heavy_view<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.cnt.p, cv.inv_off.p, cv.g_idx.p, U, cv.g_list.p,
+                                                            cv.g_cnt.p, cv.g_rng.p);
+        count_launch();
+        k_heavy_entries<<<grid_for((size_t)cv.entries, 256, 8192), 256, 0, s>>>(cv.entry_uidx.p, cv.g_idx.p,
+                                                                               (uint32_t)cv.entries, cv.g_entry.p);
+        HSAW_CK(cudaGetLastError());
+        GreedyView Vh;
+        Vh.U = H;
+        Vh.cnt = cv.g_cnt.p;
+        Vh.rng = cv.g_rng.p;
+        Vh.eidx = cv.g_entry.p;
+        st = cluster_greedy(cv, Vh, k, 2u, outs.p, outs.p + k, ctl, &rounds, &heavy_done, s);
+        if (st == HSAW_OK && heavy_done && rounds > 0) {
+          count_launch();
+          k_map_picks<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(outs.p, rounds, cv.g_list.p);
+          if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: pick map launch failed");
+        }
+        if (st == HSAW_OK && heavy_done) {
+          done = true;
+          if (rounds < k) {  // every remaining gain is below 2: all elements, counts over the uncovered walks
+            count_launch();
+            k_recount<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.inv_off.p, cv.inv_walk.p, cv.covered.p, U,
+                                                             cand_dev, cv.cnt_work.p);
+            if (rounds > 0) {
+              count_launch();
+              k_exclude_picks<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(outs.p, rounds, cv.cnt_work.p);
+            }
+            count_launch();
+            k_ranges<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.inv_off.p, U, cv.g_rng.p);
+            HSAW_CK(cudaGetLastError());
+            GreedyView V;
+            V.U = U;
+            V.cnt = cv.cnt_work.p;
+            V.rng = cv.g_rng.p;
+            V.eidx = cv.entry_uidx.p;
+            int32_t more = 0;
+            bool d2 = false;
+            HSAW_CK(cudaMemsetAsync(ctl, 0, 8 * sizeof(uint32_t), s));
+            st = cluster_greedy(cv, V, k - rounds, 1u, outs.p + rounds, outs.p + k + rounds, ctl, &more, &d2, s);
+            if (st == HSAW_OK && !d2) st = fail(HSAW_E_DEVICE, "greedy: cluster unavailable after the heavy phase");
+            rounds += more;
+          }
+          if (st == HSAW_OK && rounds > 0) {
+            count_launch();
+            k_pick_ids<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(outs.p, cv.uid.p, rounds, ids.p);
+            if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: id launch failed");
+          }
+        }
+      }
+    }
+    if (st == HSAW_OK && !done) {
+      count_launch();
+      k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);
+      count_launch();
+      k_ranges<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.inv_off.p, U, cv.g_rng.p);
+      HSAW_CK(cudaGetLastError());
+      GreedyView V;
+      V.U = U;
+      V.cnt = cv.cnt_work.p;
+      V.rng = cv.g_rng.p;
+      V.eidx = cv.entry_uidx.p;
+      st = cluster_greedy(cv, V, k, 1u, outs.p, outs.p + k, ctl, &rounds, &done, s);
+      if (st == HSAW_OK && done && rounds > 0) {
+        count_launch();
+        k_pick_ids<<<grid_for(rounds, 256, 1024), 256, 0, s>>>(outs.p, cv.uid.p, rounds, ids.p);
+        if (cudaGetLastError() != cudaSuccess) st = fail(HSAW_E_DEVICE, "greedy: id launch failed");
+      }
     }
   }
   if (st == HSAW_OK && !done && U > 0 && cv.walks > 0) {
