@@ -298,7 +298,7 @@ struct GreedyParams {
   const uint32_t* inv_walk;
   const uint32_t* walk_eoff;
   const uint32_t* entry_uidx;
-  uint8_t* covered;
+  uint32_t* covered;         // per walk: nonzero once covered
   unsigned long long* gkey;  // NG: cached largest key of each group
   uint8_t* dirty;            // NG
   unsigned long long* partial;  // gridDim.x
@@ -437,300 +437,320 @@ __global__ void __launch_bounds__(512) k_greedy(GreedyParams P) {
 }
 
 // ------------------------------------------------------------------ greedy on one cluster
-// The same greedy on one thread-block cluster.  The per-group largest keys live in the
-// CTAs' shared memory (CTA r owns groups [r * per_cta, (r + 1) * per_cta)); group g covers
-// elements [g << gshift, (g + 1) << gshift).  Counts only fall, so a group's largest key
-// changes only when the count of that key's own element changes: a thread that decrements
-// element x reads the largest key of x's group from its owner (distributed shared memory)
-// and, only if x is that key's element, marks the group stale there.  The next pick
-// rescans just the stale groups.  Each entry of the inverted index carries its walk's
-// entry range, so covering a walk needs no separate offset lookup, and the walk's first
-// element id is fetched together with its covered flag.
+// The same greedy on one thread-block cluster.  CTA r owns the elements
+// [r * epc, (r + 1) * epc), in groups of 2^gshift: the largest key of each owned group lives
+// in its shared memory, and so do the owned counts and walk-list ranges when they fit there
+// (the on-chip version; otherwise the counts stay in global memory).  Counts only fall, so
+// a group's largest key changes only when the count of that key's own element changes: a
+// decrement of x marks x's group stale only if x is the element of its largest key, and
+// the next pick rescans just the stale groups.
+//
+// A pick costs one cluster barrier: after it every CTA knows the winner and its walk-list
+// range (pushed with the winning key), reads all of the winner's walks that no earlier pick
+// covered, and takes down the counts of the elements it owns; then it rescans its stale
+// groups and pushes its largest key into every CTA's slot for the next pick (two slot
+// sets, by the pick's parity, so a CTA that runs ahead never overwrites keys a slower CTA
+// still reads).  Walks carry a stamp, 0 or 1 + the pick that covered them, so every CTA
+// takes the same walks as new (stamp 0 or this pick's).  A pick whose walks hold many
+// entries is instead covered once across the cluster: each walk by one CTA, decrements
+// sent to the owner (shared-memory atomics on chip, global atomics otherwise) together with
+// a read of the owner's group key, and a second barrier before the rescans.
 namespace cg = cooperative_groups;
-
-constexpr unsigned long long KEY_UNKNOWN = ~0ull;  // above every element key (counts < 2^31)
 
 // Entries of walk elements that the greedy does not track carry this index.
 constexpr uint32_t UNTRACKED = 0xFFFFFFFFu;
 
 struct ClusterGreedyParams {
-  uint32_t U, NG, per_cta, gshift;
-  uint32_t short_walks;  // 1: walks average few elements, cover one walk per thread
+  uint32_t U;
+  uint32_t epc;          // elements per CTA (a multiple of the group size)
+  uint32_t gshift;       // groups of 2^gshift elements
+  uint32_t ng;           // groups per CTA (epc >> gshift)
+  uint32_t short_walks;  // 1: walks average few elements, one thread per walk when covering across the cluster
   uint32_t min_gain;     // stop before a pick whose gain is below this (>= 1)
+  uint32_t owned_max;    // cover by ownership while (walks of the pick) x avg_entries is at most this
+  uint32_t avg_entries;  // walk entries per walk, rounded up
+  uint32_t tag0;         // picks of earlier runs over the same stamps
   int32_t k;
-  uint32_t* cnt;  // running counts | EXCLUDED
+  uint32_t* cnt;         // counts | EXCLUDED: the running counts, or the initial ones for the on-chip version
   const uint2* rng;      // per element: its entries [x, y) of inv_ent
   const uint4* inv_ent;  // {walk, first entry, end entry, 0} per inverted-index entry
   const uint32_t* entry_uidx;  // per walk entry: element index, or UNTRACKED
-  uint8_t* covered;
+  uint32_t* stamp;       // per walk: 0, or tag0 + 1 + the pick that covered it
   uint32_t* out_u;
   uint32_t* out_gain;
-  uint32_t* ctl;  // [3] rounds done
+  uint32_t* ctl;  // [3] rounds done, [4] picks covered across the cluster
 };
 
-// One decrement of element x: its running count, and the stale bit of its group in the
-// owner CTA when x is the element of that group's largest key.
-__device__ __forceinline__ void cover_decrement(const ClusterGreedyParams& P, cg::cluster_group& cluster,
-                                                unsigned long long* gkey, uint32_t* sbits, uint32_t x) {
-  if (x == UNTRACKED) return;
-  atomicSub(&P.cnt[x], 1u);
-  const uint32_t gg = x >> P.gshift, owner = gg / P.per_cta, gl = gg % P.per_cta;
-  const unsigned long long top = *cluster.map_shared_rank(&gkey[gl], owner);
-  if (top != 0 && 0xFFFFFFFFu - (uint32_t)top == x) {
-    uint32_t* rb = cluster.map_shared_rank(sbits, owner);
-    atomicOr(&rb[gl >> 5], 1u << (gl & 31));
-  }
-}
-
-__global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams P) {
-  extern __shared__ unsigned long long gkey[];  // per: largest key of each owned group
-  __shared__ unsigned long long red[32];
-  __shared__ unsigned long long slot[16];  // largest key of each CTA of the cluster
-  cg::cluster_group cluster = cg::this_cluster();
-  const uint32_t rank = cluster.block_rank();
-  const uint32_t C = cluster.num_blocks();
-  const uint32_t per = P.per_cta;
-  const uint32_t words = (per + 31) / 32;
-  uint32_t* sbits = reinterpret_cast<uint32_t*>(gkey + per);  // stale bits of the owned groups
+// Exclusive prefix sum of one value per thread of the block; *total gets the block's sum.
+// wsum holds 33 words.
+__device__ __forceinline__ uint32_t block_exsum(uint32_t v, uint32_t* wsum, uint32_t* total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t gbase = rank * per;
-  const uint32_t gend = min(P.NG, gbase + per);
-  const uint32_t nown = gend > gbase ? gend - gbase : 0;
-  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sbits[i] = 0xFFFFFFFFu;
-  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) gkey[i] = KEY_UNKNOWN;
-  cluster.sync();
-  const uint32_t gsz = 1u << P.gshift;
-  int32_t r = 0;
-  for (; r < P.k; ++r) {
-    // 1. rescan the owned groups marked stale, one warp per group
-    for (uint32_t wi = w; wi < words; wi += nw) {
-      uint32_t todo = sbits[wi];
-      __syncwarp();
-      if (!todo) continue;
-      if (lane == 0) sbits[wi] = 0;
-      while (todo) {
-        const uint32_t b = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint32_t gl = wi * 32 + b;
-        if (gl >= nown) continue;
-        const uint32_t e0 = (gbase + gl) << P.gshift;
-        const uint32_t e1 = min(P.U, e0 + gsz);
-        unsigned long long best = 0;
-        for (uint32_t u = e0 + lane; u < e1; u += 32) {
-          const unsigned long long key = elem_key(__ldcg(&P.cnt[u]), u);
-          best = key > best ? key : best;
-        }
-        best = warp_max_u64(best);
-        if (lane == 0) gkey[gl] = best;
-      }
-    }
-    __syncthreads();
-    // 2. cluster-wide argmax of (count, smallest id): each CTA pushes its largest key into
-    //    slot[rank] of every CTA, then every warp reduces the slots it holds
-    unsigned long long key = 0;
-    for (uint32_t gl = threadIdx.x; gl < nown; gl += blockDim.x) key = gkey[gl] > key ? gkey[gl] : key;
-    key = warp_max_u64(key);
-    if (lane == 0) red[w] = key;
-    __syncthreads();
-    if (w == 0) {
-      key = lane < nw ? red[lane] : 0ull;
-      key = warp_max_u64(key);
-      if (lane < (int)C) *cluster.map_shared_rank(&slot[rank], lane) = key;
-    }
-    cluster.sync();
-    key = lane < (int)C ? slot[lane] : 0ull;
-    key = warp_max_u64(key);
-    const uint32_t gain = (uint32_t)(key >> 32);
-    if (gain < P.min_gain) break;  // the same decision in every CTA (gain 0: every remaining gain is zero)
-    const uint32_t u = 0xFFFFFFFFu - (uint32_t)key;
-    if (rank == 0 && threadIdx.x == 0) {
-      P.out_u[r] = u;
-      P.out_gain[r] = gain;
-      atomicOr(&P.cnt[u], EXCLUDED);
-    }
-    if (threadIdx.x == 0) {  // the picked element's group is stale in its owner
-      const uint32_t gg = u >> P.gshift;
-      if (gg / per == rank) atomicOr(&sbits[(gg % per) >> 5], 1u << ((gg % per) & 31));
-    }
-    // 3. cover its walks (one thread per walk when walks are short, one warp per walk
-    //    otherwise); the group keys read by cover_decrement do not change until step 1
-    const uint2 qr = P.rng[u];
-    const uint32_t q0 = qr.x, q1 = qr.y;
-    if (P.short_walks) {
-      for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
-        const uint4 ent = __ldg(&P.inv_ent[q]);
-        const uint32_t x0 = ent.y < ent.z ? __ldg(&P.entry_uidx[ent.y]) : 0u;  // in flight with the flag
-        if (__ldcg(&P.covered[ent.x])) continue;
-        P.covered[ent.x] = 1;
-        if (ent.y < ent.z) cover_decrement(P, cluster, gkey, sbits, x0);
-        for (uint32_t p = ent.y + 1; p < ent.z; ++p) cover_decrement(P, cluster, gkey, sbits, __ldg(&P.entry_uidx[p]));
-      }
-    } else {
-      for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
-        const uint4 ent = __ldg(&P.inv_ent[q]);
-        const uint32_t p = ent.y + lane;
-        const uint32_t x = p < ent.z ? __ldg(&P.entry_uidx[p]) : 0u;  // in flight with the flag
-        uint32_t fresh = 0;
-        if (lane == 0) fresh = __ldcg(&P.covered[ent.x]) ? 0u : 1u;
-        fresh = __shfl_sync(0xffffffffu, fresh, 0);
-        if (!fresh) continue;
-        if (lane == 0) P.covered[ent.x] = 1;
-        if (p < ent.z) cover_decrement(P, cluster, gkey, sbits, x);
-        for (uint32_t pp = p + 32; pp < ent.z; pp += 32) cover_decrement(P, cluster, gkey, sbits, __ldg(&P.entry_uidx[pp]));
-      }
-    }
-    cluster.sync();
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
   }
-  cluster.sync();  // no CTA leaves while a peer may still read its shared memory
-  if (rank == 0 && threadIdx.x == 0) P.ctl[3] = (uint32_t)r;
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t s = lane < nw ? wsum[lane] : 0u;
+    uint32_t si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += y;
+    }
+    if (lane < nw) wsum[lane] = si - s;
+    if (lane == 31) wsum[32] = si;
+  }
+  __syncthreads();
+  *total = wsum[32];
+  return wsum[w] + inc - v;
 }
 
-// ------------------------------------------------------------------ greedy with on-chip counts
-// When the running counts and inverted-index offsets of all touched elements fit in the
-// cluster's shared memory (about 26 K elements per CTA), CTA r owns elements
-// [r * per, (r + 1) * per): their counts, their walk-list offsets, and the largest key of
-// each 32-element group, all in its shared memory.  A CTA's candidate for the argmax
-// carries its walk-list range, so once the winner is known every CTA starts covering
-// without a global-memory lookup; decrements are atomics on the owner's shared memory
-// (distributed shared memory), with the stale mark as in k_greedy_cluster; rescans read
-// shared memory only.
-struct OnchipGreedyParams {
-  uint32_t U, per;        // elements, elements per CTA
-  uint32_t short_walks;
-  uint32_t min_gain;      // stop before a pick whose gain is below this (>= 1)
-  int32_t k;
-  const uint32_t* cnt0;   // initial counts | EXCLUDED (U)
-  const uint2* rng;       // U: each element's entries [x, y) of inv_ent
-  const uint4* inv_ent;
-  const uint32_t* entry_uidx;  // per walk entry: element index, or UNTRACKED
-  uint8_t* covered;
-  uint32_t* out_u;
-  uint32_t* out_gain;
-  uint32_t* ctl;  // [3] rounds done
+template <bool ONCHIP>
+struct ClusterGreedyState {
+  const ClusterGreedyParams& P;
+  cg::cluster_group& cluster;
+  unsigned long long* gkey;  // ng: largest key of each owned group
+  unsigned long long* wmax;  // (ng + 31) / 32: largest key of each 32 groups
+  uint2* rng_s;              // on chip: epc walk-list ranges
+  uint32_t* cnt_s;           // on chip: epc counts
+  uint32_t* sbits;           // stale bits of the owned groups
+  uint32_t lo;               // first owned element
+
+  __device__ __forceinline__ uint32_t count(uint32_t lx) const {
+    return ONCHIP ? cnt_s[lx] : __ldcg(&P.cnt[lo + lx]);
+  }
+  __device__ __forceinline__ void mark(uint32_t* bits, uint32_t gl) const { atomicOr(&bits[gl >> 5], 1u << (gl & 31)); }
+  // one decrement of an owned element x (lx = x - lo)
+  __device__ __forceinline__ void dec_owned(uint32_t x, uint32_t lx) const {
+    if (ONCHIP)
+      atomicSub(&cnt_s[lx], 1u);
+    else
+      atomicSub(&P.cnt[x], 1u);
+    const uint32_t gl = lx >> P.gshift;
+    const unsigned long long top = gkey[gl];
+    if (top != 0 && 0xFFFFFFFFu - (uint32_t)top == x) mark(sbits, gl);
+  }
+  // one decrement of any element x, at its owner
+  __device__ __forceinline__ void dec_remote(uint32_t x) const {
+    if (x == UNTRACKED) return;
+    const uint32_t owner = x / P.epc, lx = x - owner * P.epc, gl = lx >> P.gshift;
+    if (ONCHIP)
+      atomicSub(cluster.map_shared_rank(&cnt_s[lx], owner), 1u);
+    else
+      atomicSub(&P.cnt[x], 1u);
+    const unsigned long long top = *cluster.map_shared_rank(&gkey[gl], owner);
+    if (top != 0 && 0xFFFFFFFFu - (uint32_t)top == x) mark(cluster.map_shared_rank(sbits, owner), gl);
+  }
 };
 
-constexpr uint32_t ONCHIP_GROUP = 32;
-
-__device__ __forceinline__ void onchip_decrement(const OnchipGreedyParams& P, cg::cluster_group& cluster,
-                                                 uint32_t* cnt_s, unsigned long long* gkey, uint32_t* sbits,
-                                                 uint32_t x) {
-  if (x == UNTRACKED) return;
-  const uint32_t owner = x / P.per, lx = x - owner * P.per, gl = lx / ONCHIP_GROUP;
-  atomicSub(cluster.map_shared_rank(&cnt_s[lx], owner), 1u);
-  const unsigned long long top = *cluster.map_shared_rank(&gkey[gl], owner);
-  if (top != 0 && 0xFFFFFFFFu - (uint32_t)top == x)
-    atomicOr(cluster.map_shared_rank(&sbits[gl >> 5], owner), 1u << (gl & 31));
-}
-
-__global__ void __launch_bounds__(1024, 1) k_greedy_onchip(OnchipGreedyParams P) {
+template <bool ONCHIP>
+__device__ __forceinline__ void greedy_cluster_body(const ClusterGreedyParams& P) {
   extern __shared__ unsigned long long smem_u64[];
   __shared__ unsigned long long red[32];
-  __shared__ unsigned long long slot_key[16];
-  __shared__ unsigned long long slot_rng[16];  // walk-list range (q0 << 32 | q1) of each CTA's candidate
+  __shared__ ulonglong2 slot[2][16];  // by pick parity, per CTA: {largest key, its walk range q0 << 32 | q1}
+  __shared__ uint32_t wy[1024];       // cover by ownership: first entry of each new walk of the pass
+  __shared__ uint32_t woff[1025];     // and the new walks' entry offsets (woff[n] = all entries)
+  __shared__ uint32_t wsum[33];
   cg::cluster_group cluster = cg::this_cluster();
   const uint32_t rank = cluster.block_rank();
   const uint32_t C = cluster.num_blocks();
-  const uint32_t per = P.per;
-  const uint32_t ng = (per + ONCHIP_GROUP - 1) / ONCHIP_GROUP;
-  const uint32_t words = (ng + 31) / 32;
-  unsigned long long* gkey = smem_u64;                       // ng
-  uint2* rng_s = reinterpret_cast<uint2*>(gkey + ng);        // per
-  uint32_t* cnt_s = reinterpret_cast<uint32_t*>(rng_s + per);  // per
-  uint32_t* sbits = cnt_s + per;                             // words
+  const uint32_t ng = P.ng, words = (ng + 31) / 32, epc = P.epc;
+  const uint32_t lo = rank * epc;
+  const uint32_t own = P.U > lo ? min(epc, P.U - lo) : 0u;
+  ClusterGreedyState<ONCHIP> S{P, cluster, smem_u64, smem_u64 + ng, nullptr, nullptr, nullptr, lo};
+  S.rng_s = reinterpret_cast<uint2*>(S.wmax + words);
+  S.cnt_s = reinterpret_cast<uint32_t*>(S.rng_s + (ONCHIP ? epc : 0u));
+  S.sbits = S.cnt_s + (ONCHIP ? epc : 0u);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t base = rank * per;
-  const uint32_t own = P.U > base ? min(per, P.U - base) : 0;
-  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) cnt_s[i] = i < own ? P.cnt0[base + i] : EXCLUDED;
-  for (uint32_t i = threadIdx.x; i < own; i += blockDim.x) rng_s[i] = P.rng[base + i];
-  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sbits[i] = 0xFFFFFFFFu;
-  for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) gkey[i] = 0;
+  if (ONCHIP) {
+    for (uint32_t i = threadIdx.x; i < epc; i += blockDim.x) S.cnt_s[i] = i < own ? P.cnt[lo + i] : EXCLUDED;
+    for (uint32_t i = threadIdx.x; i < own; i += blockDim.x) S.rng_s[i] = P.rng[lo + i];
+  }
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) S.sbits[i] = 0xFFFFFFFFu;
+  for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) S.gkey[i] = 0ull;
   cluster.sync();
+  const uint32_t gsz = 1u << P.gshift;
+  uint32_t q0 = 0, q1 = 0;  // the previous pick's walk-list range
+  bool owned = true;
+  uint32_t spread = 0;  // picks covered across the cluster
   int32_t r = 0;
   for (; r < P.k; ++r) {
-    // 1. rescan the stale groups from shared memory, one warp per group, one element per lane
+    // 1. cover the previous pick's walks
+    if (r > 0) {
+      const uint32_t tag = P.tag0 + (uint32_t)r;
+      if (owned) {
+        for (uint32_t b0 = q0; b0 < q1; b0 += blockDim.x) {
+          const uint32_t n = min((uint32_t)blockDim.x, q1 - b0);
+          uint32_t y = 0, len = 0;
+          if (threadIdx.x < n) {
+            const uint4 ent = __ldg(&P.inv_ent[b0 + threadIdx.x]);
+            const uint32_t s = __ldcg(&P.stamp[ent.x]);
+            if (s == 0u || s == tag) {
+              y = ent.y;
+              len = ent.z - ent.y;
+              if (s == 0u && rank == 0) P.stamp[ent.x] = tag;
+            }
+          }
+          uint32_t total = 0;
+          const uint32_t off = block_exsum(len, wsum, &total);
+          if (threadIdx.x < n) {
+            wy[threadIdx.x] = y;
+            woff[threadIdx.x] = off;
+          }
+          if (threadIdx.x == 0) woff[n] = total;
+          __syncthreads();
+          // thread t takes the entry positions [t c, (t + 1) c) of the new walks, in order
+          const uint32_t c = (total + blockDim.x - 1) / blockDim.x;
+          const uint64_t f64 = (uint64_t)threadIdx.x * c;
+          uint32_t f = (uint32_t)(f64 < total ? f64 : (uint64_t)total);
+          const uint32_t fend = (uint32_t)(f64 + c < total ? f64 + c : (uint64_t)total);
+          if (f < fend) {
+            uint32_t a = 0, b = n;  // the walk holding position f: the last i < n with woff[i] <= f
+            while (b - a > 1) {
+              const uint32_t m = (a + b) >> 1;
+              if (woff[m] <= f) a = m; else b = m;
+            }
+            uint32_t i = a, nxt = woff[a + 1], at = wy[a] - woff[a];  // position f is entry at + f
+            while (f < fend) {
+              uint32_t xs[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                xs[j] = UNTRACKED;
+                if (f < fend) {
+                  while (f >= nxt) {
+                    ++i;
+                    nxt = woff[i + 1];
+                    at = wy[i] - woff[i];
+                  }
+                  xs[j] = __ldg(&P.entry_uidx[at + f]);
+                  ++f;
+                }
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const uint32_t lx = xs[j] - lo;
+                if (xs[j] != UNTRACKED && lx < epc) S.dec_owned(xs[j], lx);
+              }
+            }
+          }
+          __syncthreads();  // wy, woff and wsum are reused by the next pass
+        }
+      } else {
+        ++spread;
+        if (P.short_walks) {
+          for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
+            const uint4 ent = __ldg(&P.inv_ent[q]);
+            const uint32_t x0 = ent.y < ent.z ? __ldg(&P.entry_uidx[ent.y]) : 0u;  // in flight with the stamp
+            if (__ldcg(&P.stamp[ent.x])) continue;
+            P.stamp[ent.x] = tag;
+            if (ent.y < ent.z) S.dec_remote(x0);
+            for (uint32_t p = ent.y + 1; p < ent.z; ++p) S.dec_remote(__ldg(&P.entry_uidx[p]));
+          }
+        } else {
+          for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
+            const uint4 ent = __ldg(&P.inv_ent[q]);
+            const uint32_t p = ent.y + lane;
+            const uint32_t x = p < ent.z ? __ldg(&P.entry_uidx[p]) : 0u;  // in flight with the stamp
+            uint32_t fresh = 0;
+            if (lane == 0) fresh = __ldcg(&P.stamp[ent.x]) ? 0u : 1u;
+            fresh = __shfl_sync(0xffffffffu, fresh, 0);
+            if (!fresh) continue;
+            if (lane == 0) P.stamp[ent.x] = tag;
+            if (p < ent.z) S.dec_remote(x);
+            for (uint32_t pp = p + 32; pp < ent.z; pp += 32) S.dec_remote(__ldg(&P.entry_uidx[pp]));
+          }
+        }
+        cluster.sync();  // every decrement and stale mark is in place before the rescans
+      }
+    }
+    __syncthreads();
+    // 2. rescan the owned groups marked stale, one warp per group
     for (uint32_t wi = w; wi < words; wi += nw) {
-      uint32_t todo = sbits[wi];
+      uint32_t todo = S.sbits[wi];
       __syncwarp();
       if (!todo) continue;
-      if (lane == 0) sbits[wi] = 0;
+      if (lane == 0) S.sbits[wi] = 0;
       while (todo) {
         const uint32_t gl = wi * 32 + __ffs(todo) - 1;
         todo &= todo - 1;
-        const uint32_t lx = gl * ONCHIP_GROUP + lane;
-        unsigned long long key = lx < per ? elem_key(cnt_s[lx], base + lx) : 0ull;
-        key = warp_max_u64(key);
-        if (lane == 0 && gl < ng) gkey[gl] = key;
+        if (gl >= ng) continue;
+        const uint32_t e0 = gl << P.gshift;
+        const uint32_t e1 = min(own, e0 + gsz);
+        unsigned long long best = 0;
+        for (uint32_t lx = e0 + lane; lx < e1; lx += 32) {
+          const unsigned long long key = elem_key(S.count(lx), lo + lx);
+          best = key > best ? key : best;
+        }
+        best = warp_max_u64(best);
+        if (lane == 0) S.gkey[gl] = best;
       }
+      __syncwarp();
+      const uint32_t gl = wi * 32 + lane;
+      const unsigned long long m = warp_max_u64(gl < ng ? S.gkey[gl] : 0ull);
+      if (lane == 0) S.wmax[wi] = m;
     }
     __syncthreads();
-    // 2. this CTA's candidate with its walk-list range, pushed into every CTA's slots
+    // 3. this CTA's largest key with its walk-list range, pushed into every CTA's slot
     unsigned long long key = 0;
-    for (uint32_t gl = threadIdx.x; gl < ng; gl += blockDim.x) key = gkey[gl] > key ? gkey[gl] : key;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) key = S.wmax[i] > key ? S.wmax[i] : key;
     key = warp_max_u64(key);
     if (lane == 0) red[w] = key;
     __syncthreads();
+    const int par = r & 1;
     if (w == 0) {
       key = lane < nw ? red[lane] : 0ull;
       key = warp_max_u64(key);
-      unsigned long long rng = 0;
+      unsigned long long qr = 0;
       if (key) {
-        const uint2 qr = rng_s[0xFFFFFFFFu - (uint32_t)key - base];
-        rng = ((unsigned long long)qr.x << 32) | qr.y;
+        const uint32_t u = 0xFFFFFFFFu - (uint32_t)key;
+        const uint2 g = ONCHIP ? S.rng_s[u - lo] : __ldg(&P.rng[u]);
+        qr = ((unsigned long long)g.x << 32) | g.y;
       }
-      if (lane < (int)C) {
-        *cluster.map_shared_rank(&slot_key[rank], lane) = key;
-        *cluster.map_shared_rank(&slot_rng[rank], lane) = rng;
-      }
+      if (lane < (int)C) *cluster.map_shared_rank(&slot[par][rank], lane) = make_ulonglong2(key, qr);
     }
     cluster.sync();
-    key = lane < (int)C ? slot_key[lane] : 0ull;
-    const unsigned long long best = warp_max_u64(key);
+    // 4. the cluster's largest key: the pick (the same in every CTA)
+    const unsigned long long mine = lane < (int)C ? slot[par][lane].x : 0ull;
+    const unsigned long long best = warp_max_u64(mine);
     const uint32_t gain = (uint32_t)(best >> 32);
     if (gain < P.min_gain) break;  // the same decision in every CTA (gain 0: every remaining gain is zero)
     const uint32_t u = 0xFFFFFFFFu - (uint32_t)best;
-    const uint32_t winner = u / per;
-    const unsigned long long rng = slot_rng[winner];
-    const uint32_t q0 = (uint32_t)(rng >> 32), q1 = (uint32_t)rng;
+    const int src = __ffs(__ballot_sync(0xffffffffu, lane < (int)C && mine == best)) - 1;
+    const unsigned long long qr = slot[par][src].y;
+    q0 = (uint32_t)(qr >> 32);
+    q1 = (uint32_t)qr;
+    owned = (unsigned long long)(q1 - q0) * P.avg_entries <= P.owned_max;
     if (rank == 0 && threadIdx.x == 0) {
       P.out_u[r] = u;
       P.out_gain[r] = gain;
     }
-    if (rank == winner && threadIdx.x == 0) {  // the picked element leaves the candidates
-      const uint32_t lx = u - base;
-      atomicOr(&cnt_s[lx], EXCLUDED);
-      atomicOr(&sbits[(lx / ONCHIP_GROUP) >> 5], 1u << ((lx / ONCHIP_GROUP) & 31));
+    if (u - lo < epc && threadIdx.x == 0) {  // the owner takes the pick out of the candidates
+      if (ONCHIP)
+        atomicOr(&S.cnt_s[u - lo], EXCLUDED);
+      else
+        atomicOr(&P.cnt[u], EXCLUDED);
+      S.mark(S.sbits, (u - lo) >> P.gshift);
     }
-    // 3. cover its walks; the group keys read by onchip_decrement do not change until step 1
-    if (P.short_walks) {
-      for (uint32_t q = q0 + rank * blockDim.x + threadIdx.x; q < q1; q += C * blockDim.x) {
-        const uint4 ent = __ldg(&P.inv_ent[q]);
-        const uint32_t x0 = ent.y < ent.z ? __ldg(&P.entry_uidx[ent.y]) : 0u;  // in flight with the flag
-        if (__ldcg(&P.covered[ent.x])) continue;
-        P.covered[ent.x] = 1;
-        if (ent.y < ent.z) onchip_decrement(P, cluster, cnt_s, gkey, sbits, x0);
-        for (uint32_t p = ent.y + 1; p < ent.z; ++p)
-          onchip_decrement(P, cluster, cnt_s, gkey, sbits, __ldg(&P.entry_uidx[p]));
-      }
-    } else {
-      for (uint32_t q = q0 + rank * nw + w; q < q1; q += C * nw) {
-        const uint4 ent = __ldg(&P.inv_ent[q]);
-        const uint32_t p = ent.y + lane;
-        const uint32_t x = p < ent.z ? __ldg(&P.entry_uidx[p]) : 0u;  // in flight with the flag
-        uint32_t fresh = 0;
-        if (lane == 0) fresh = __ldcg(&P.covered[ent.x]) ? 0u : 1u;
-        fresh = __shfl_sync(0xffffffffu, fresh, 0);
-        if (!fresh) continue;
-        if (lane == 0) P.covered[ent.x] = 1;
-        if (p < ent.z) onchip_decrement(P, cluster, cnt_s, gkey, sbits, x);
-        for (uint32_t pp = p + 32; pp < ent.z; pp += 32)
-          onchip_decrement(P, cluster, cnt_s, gkey, sbits, __ldg(&P.entry_uidx[pp]));
-      }
-    }
-    cluster.sync();
   }
   cluster.sync();  // no CTA leaves while a peer may still read its shared memory
-  if (rank == 0 && threadIdx.x == 0) P.ctl[3] = (uint32_t)r;
+  if (rank == 0 && threadIdx.x == 0) {
+    P.ctl[3] = (uint32_t)r;
+    P.ctl[4] = spread;
+  }
 }
+
+__global__ void __launch_bounds__(1024, 1) k_greedy_cluster(ClusterGreedyParams P) { greedy_cluster_body<false>(P); }
+
+// The on-chip version: when the counts and walk-list ranges of all elements fit in the
+// cluster's shared memory (about 17 K elements per CTA), decrements and rescans stay on chip
+// and a CTA's candidate travels with its range, so covering starts without a global lookup.
+constexpr uint32_t ONCHIP_GROUP = 32;
+
+__global__ void __launch_bounds__(1024, 1) k_greedy_onchip(ClusterGreedyParams P) { greedy_cluster_body<true>(P); }
 
 // Inverted-index entries with their walk's entry range: {j, walk_eoff[j], walk_eoff[j + 1], 0}.
 __global__ void k_inv_ranges(const uint32_t* __restrict__ inv_walk, const uint32_t* __restrict__ walk_eoff, uint32_t E,
@@ -845,22 +865,50 @@ static ClusterCfg cluster_cfg_for(Kernel kernel) {
 
 // The elements a cluster greedy works on: U of them with running counts (| EXCLUDED), each
 // element's entries [x, y) of cv.inv_ent, and per walk entry the element's index (or
-// UNTRACKED).  The caller sets up the counts and clears the covered flags.
+// UNTRACKED).  The caller sets up the counts and clears the walk stamps (or, for a second
+// run over walks the first one partly covered, gives the first run's picks as tag0).
 struct GreedyView {
   uint32_t U = 0;
+  uint32_t tag0 = 0;  // picks already made over the same walk stamps
   uint32_t* cnt = nullptr;
   const uint2* rng = nullptr;
   const uint32_t* eidx = nullptr;
 };
 
 static void log_greedy(const char* kind, const Cover& cv, const GreedyView& V, uint32_t csize, const char* what,
-                       uint32_t size, int32_t k, cudaEvent_t ev0, cudaEvent_t ev1) {
+                       uint32_t size, int32_t k, const uint32_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
-  fprintf(stderr, "hsaw: %s walks=%lld entries=%lld unique=%u cluster=%u %s=%u k=%d ms=%.3f\n", kind,
-          (long long)cv.walks, (long long)cv.entries, V.U, csize, what, size, k, ms);
+  fprintf(stderr, "hsaw: %s walks=%lld entries=%lld unique=%u cluster=%u %s=%u k=%d picks=%u spread=%u ms=%.3f\n",
+          kind, (long long)cv.walks, (long long)cv.entries, V.U, csize, what, size, k, h[3], h[4], ms);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
+}
+
+// The launch parameters both cluster versions share; the caller sets the ownership (epc,
+// gshift, ng).  HSAW_GREEDY_OWNED_MAX overrides the largest pick, in walk entries, that
+// every CTA covers by ownership (a measurement aid).
+static ClusterGreedyParams greedy_params(const Cover& cv, const GreedyView& V, int32_t k, uint32_t min_gain,
+                                         bool short_walks, uint32_t* out_u, uint32_t* out_gain, uint32_t* ctl) {
+  const char* e = getenv("HSAW_GREEDY_OWNED_MAX");
+  const uint32_t owned_max = e ? (uint32_t)strtoul(e, nullptr, 10) : 16384u;
+  ClusterGreedyParams P = {};
+  P.U = V.U;
+  P.short_walks = short_walks ? 1u : 0u;
+  P.min_gain = min_gain;
+  P.owned_max = owned_max;
+  P.avg_entries = cv.walks > 0 ? (uint32_t)std::max<int64_t>(1, (cv.entries + cv.walks - 1) / cv.walks) : 1u;
+  P.tag0 = V.tag0;
+  P.k = k;
+  P.cnt = V.cnt;
+  P.rng = V.rng;
+  P.inv_ent = cv.inv_ent.p;
+  P.entry_uidx = V.eidx;
+  P.stamp = cv.covered.p;
+  P.out_u = out_u;
+  P.out_gain = out_gain;
+  P.ctl = ctl;
+  return P;
 }
 
 // The greedy with on-chip counts when one cluster's shared memory holds every element's
@@ -873,27 +921,17 @@ static hsaw_status onchip_greedy(Cover& cv, const GreedyView& V, int32_t k, uint
   const uint32_t U = V.U;
   auto need = [](uint32_t per) {
     const size_t ng = (per + ONCHIP_GROUP - 1) / ONCHIP_GROUP;
-    return ng * 8 + (size_t)per * 8 + (size_t)per * 4 + (ng + 31) / 32 * 4 + 64;
+    return ng * 8 + (ng + 31) / 32 * 12 + (size_t)per * 8 + (size_t)per * 4 + 64;
   };
   auto per_for = [U](uint32_t c) { return (uint32_t)(((uint64_t)U + c - 1) / c + 31) / 32 * 32; };
   csize = std::min<uint32_t>(std::max<uint32_t>(csize, 1), (uint32_t)cfg1.size);
   while (need(per_for(csize)) > cfg1.smem_cap && (int)csize < cfg1.size) csize *= 2;
   const uint32_t per = per_for(csize);
   if (need(per) > cfg1.smem_cap) return HSAW_OK;
-  OnchipGreedyParams P;
-  P.U = U;
-  P.per = per;
-  P.short_walks = short_walks ? 1u : 0u;
-  P.min_gain = min_gain;
-  P.k = k;
-  P.cnt0 = V.cnt;
-  P.rng = V.rng;
-  P.inv_ent = cv.inv_ent.p;
-  P.entry_uidx = V.eidx;
-  P.covered = cv.covered.p;
-  P.out_u = out_u;
-  P.out_gain = out_gain;
-  P.ctl = ctl;
+  ClusterGreedyParams P = greedy_params(cv, V, k, min_gain, short_walks, out_u, out_gain, ctl);
+  P.epc = per;
+  P.gshift = 5;
+  P.ng = per / ONCHIP_GROUP;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -915,11 +953,11 @@ static hsaw_status onchip_greedy(Cover& cv, const GreedyView& V, int32_t k, uint
   }
   count_launch();
   HSAW_CK(cudaLaunchKernelEx(&cfg, k_greedy_onchip, P));
-  uint32_t h[4];
-  HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
+  uint32_t h[8];
+  HSAW_CK(cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
   if (log) cudaEventRecord(ev1, s);
   HSAW_CK(cudaStreamSynchronize(s));
-  if (log) log_greedy("k_greedy_onchip", cv, V, csize, "per", per, k, ev0, ev1);
+  if (log) log_greedy("k_greedy_onchip", cv, V, csize, "per", per, k, h, ev0, ev1);
   *rounds = (int32_t)h[3];
   *done = true;
   return HSAW_OK;
@@ -941,7 +979,7 @@ static hsaw_status cluster_greedy(Cover& cv, const GreedyView& V, int32_t k, uin
   const uint32_t U = V.U;
   // a cluster whose shared memory holds the keys of 256-element groups; beyond the largest
   // cluster, larger groups
-  auto need = [](uint32_t per) { return (size_t)per * 8 + ((size_t)per + 31) / 32 * 4 + 64; };
+  auto need = [](uint32_t per) { return (size_t)per * 8 + ((size_t)per + 31) / 32 * 12 + 64; };
   uint32_t gshift = 8, csize = 1;
   uint32_t NG = (uint32_t)(((uint64_t)U + 255) >> 8), per = NG;
   // more CTAs (more warps to cover walks and refresh the groups they touch) for larger
@@ -974,22 +1012,10 @@ static hsaw_status cluster_greedy(Cover& cv, const GreedyView& V, int32_t k, uin
     NG = ng2;
     per = per2;
   }
-  ClusterGreedyParams P;
-  P.U = U;
-  P.NG = NG;
-  P.per_cta = per;
+  ClusterGreedyParams P = greedy_params(cv, V, k, min_gain, short_walks, out_u, out_gain, ctl);
+  P.epc = per << gshift;
   P.gshift = gshift;
-  P.short_walks = short_walks ? 1u : 0u;
-  P.min_gain = min_gain;
-  P.k = k;
-  P.cnt = V.cnt;
-  P.rng = V.rng;
-  P.inv_ent = cv.inv_ent.p;
-  P.entry_uidx = V.eidx;
-  P.covered = cv.covered.p;
-  P.out_u = out_u;
-  P.out_gain = out_gain;
-  P.ctl = ctl;
+  P.ng = per;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1011,11 +1037,11 @@ static hsaw_status cluster_greedy(Cover& cv, const GreedyView& V, int32_t k, uin
   }
   count_launch();
   HSAW_CK(cudaLaunchKernelEx(&cfg, k_greedy_cluster, P));
-  uint32_t h[4];
-  HSAW_CK(cudaMemcpyAsync(h, ctl, 16, cudaMemcpyDeviceToHost, s));
+  uint32_t h[8];
+  HSAW_CK(cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
   if (log) cudaEventRecord(ev1, s);
   HSAW_CK(cudaStreamSynchronize(s));
-  if (log) log_greedy("k_greedy_cluster", cv, V, csize, "gshift", gshift, k, ev0, ev1);
+  if (log) log_greedy("k_greedy_cluster", cv, V, csize, "gshift", gshift, k, h, ev0, ev1);
   *rounds = (int32_t)h[3];
   *done = true;
   return HSAW_OK;
@@ -1068,7 +1094,7 @@ __global__ void k_map_picks(uint32_t* __restrict__ out_u, int32_t r, const uint3
 
 // counts over the walks not covered yet (| EXCLUDED for non-candidates and picked elements)
 __global__ void k_recount(const int32_t* __restrict__ uid, const uint32_t* __restrict__ inv_off,
-                          const uint32_t* __restrict__ inv_walk, const uint8_t* __restrict__ covered, uint32_t U,
+                          const uint32_t* __restrict__ inv_walk, const uint32_t* __restrict__ covered, uint32_t U,
                           const uint8_t* __restrict__ cand, uint32_t* __restrict__ cnt_work) {
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
     uint32_t c = 0;
@@ -1100,7 +1126,7 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
     HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
     HSAW_TRY(cv.inv_ent.ensure((size_t)cv.entries, s));
     HSAW_TRY(cv.g_rng.ensure(U, s));
-    HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
+    HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks * sizeof(uint32_t), s));
     count_launch();
     k_inv_ranges<<<grid_for((size_t)cv.entries, 256, 8192), 256, 0, s>>>(cv.inv_walk.p, cv.walk_eoff.p,
                                                                         (uint32_t)cv.entries, cv.inv_ent.p);
@@ -1158,6 +1184,7 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
             V.cnt = cv.cnt_work.p;
             V.rng = cv.g_rng.p;
             V.eidx = cv.entry_uidx.p;
+            V.tag0 = (uint32_t)rounds;
             int32_t more = 0;
             bool d2 = false;
             HSAW_CK(cudaMemsetAsync(ctl, 0, 8 * sizeof(uint32_t), s));
@@ -1199,7 +1226,7 @@ hsaw_status cover_greedy(Cover& cv, const uint8_t* cand_dev, int64_t M, int32_t 
     HSAW_TRY(cv.dirty.ensure(NG, s));
     HSAW_TRY(cv.covered.ensure((size_t)cv.walks, s));
     HSAW_TRY(cv.partial.ensure((size_t)G + NG, s));
-    HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks, s));
+    HSAW_CK(cudaMemsetAsync(cv.covered.p, 0, (size_t)cv.walks * sizeof(uint32_t), s));
     HSAW_CK(cudaMemsetAsync(cv.dirty.p, 1, NG, s));
     count_launch();
     k_greedy_init<<<grid_for(U, 256, 8192), 256, 0, s>>>(cv.uid.p, cv.cnt.p, U, cand_dev, cv.cnt_work.p);

@@ -67,7 +67,8 @@ struct Cover {
   DBuf<uint32_t> entry_uidx;                // entries: unique index of each walk entry
   DBuf<uint32_t> walk_eoff;                 // walks + 1: entry offsets of the walks
   DBuf<uint32_t> cnt_work;                  // greedy's running counts
-  DBuf<uint8_t> covered, dirty;  // greedy: walk covered flags, group dirty flags
+  DBuf<uint32_t> covered;  // greedy: per walk, 0 or 1 + the pick that covered it
+  DBuf<uint8_t> dirty;     // greedy (grid version): group dirty flags
   DBuf<uint4> inv_ent;           // cluster greedy: inverted-index entries with their walk's entry range
   DBuf<uint32_t> g_idx, g_list, g_cnt, g_entry;  // greedy on the heavy elements: index map, list, counts, entries
   DBuf<uint2> g_rng;             // greedy: each element's entries of inv_ent
