@@ -233,6 +233,35 @@ enum { PH_SAMPLE = 0, PH_COUNT = 1, PH_GREEDY = 2, PH_COVERAGE = 3 };
 void* phase_begin(cudaStream_t s);
 void phase_end(void* token, cudaStream_t s, int phase);
 
+// ------------------------------------------------------------------ walk-record steps
+// The live in-edge e of a node with record rec = {first in-edge, in-degree, equal weight or
+// 0, in-sum} for a draw r < rec.w, read through the walk records (the same choice as
+// pick_in_edge: j = r / w at equal weights, otherwise the first j with r < thr[j], found
+// from the guide bucket's candidate onward).  ra, rb receive e's walk record: the tail is
+// ra.x and its node record is {ra.y, ra.z, ra.w, rb.x}.
+__device__ __forceinline__ uint32_t record_step(const uint4* __restrict__ erec, const uint4* __restrict__ grec,
+                                                uint4 rec, uint32_t r, uint4& ra, uint4& rb) {
+  uint32_t e;
+  if (rec.z) {
+    e = rec.x + r / rec.z;
+    ra = __ldg(&erec[2 * (size_t)e]);
+    rb = __ldg(&erec[2 * (size_t)e + 1]);
+  } else {
+    const size_t gp = 2 * ((size_t)rec.x + guide_bucket(r, rec.y, rec.w));
+    ra = __ldg(&grec[gp]);
+    rb = __ldg(&grec[gp + 1]);
+    e = rec.x + rb.z;
+    if (r >= rb.y) {
+      do {
+        ++e;
+        rb = __ldg(&erec[2 * (size_t)e + 1]);
+      } while (r >= rb.y);
+      ra = __ldg(&erec[2 * (size_t)e]);
+    }
+  }
+  return e;
+}
+
 }  // namespace hsaw
 
 // Opaque handle types of the ABI.

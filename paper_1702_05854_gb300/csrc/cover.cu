@@ -574,6 +574,9 @@ __device__ __forceinline__ void greedy_cluster_body(const ClusterGreedyParams& P
   for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) S.gkey[i] = 0ull;
   cluster.sync();
   const uint32_t gsz = 1u << P.gshift;
+  // with more than two groups per thread, keep the largest key of every 32 groups too, so
+  // the per-pick scan reads those and only rescanned words are refreshed
+  const bool word_max = ng > 2 * blockDim.x;
   uint32_t q0 = 0, q1 = 0;  // the previous pick's walk-list range
   bool owned = true;
   uint32_t spread = 0;  // picks covered across the cluster
@@ -688,15 +691,20 @@ __device__ __forceinline__ void greedy_cluster_body(const ClusterGreedyParams& P
         best = warp_max_u64(best);
         if (lane == 0) S.gkey[gl] = best;
       }
-      __syncwarp();
-      const uint32_t gl = wi * 32 + lane;
-      const unsigned long long m = warp_max_u64(gl < ng ? S.gkey[gl] : 0ull);
-      if (lane == 0) S.wmax[wi] = m;
+      if (word_max) {
+        __syncwarp();
+        const uint32_t gl = wi * 32 + lane;
+        const unsigned long long m = warp_max_u64(gl < ng ? S.gkey[gl] : 0ull);
+        if (lane == 0) S.wmax[wi] = m;
+      }
     }
     __syncthreads();
     // 3. this CTA's largest key with its walk-list range, pushed into every CTA's slot
     unsigned long long key = 0;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) key = S.wmax[i] > key ? S.wmax[i] : key;
+    if (word_max)
+      for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) key = S.wmax[i] > key ? S.wmax[i] : key;
+    else
+      for (uint32_t gl = threadIdx.x; gl < ng; gl += blockDim.x) key = S.gkey[gl] > key ? S.gkey[gl] : key;
     key = warp_max_u64(key);
     if (lane == 0) red[w] = key;
     __syncthreads();

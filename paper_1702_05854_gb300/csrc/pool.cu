@@ -176,22 +176,25 @@ __global__ void k_bits_emit(const uint32_t* __restrict__ bits, const uint32_t* _
 // Length of each pooled hit: nodes walked up to and including its first real source.  A
 // walk that meets no source first (impossible for an attempt the index lists) sets bit 2.
 template <bool HAS_P>
-__global__ void k_hit_len(const uint4* __restrict__ node, const uint2* __restrict__ edge, uint32_t n, uint32_t k0,
-                          uint32_t k1, const uint32_t* __restrict__ s_bits, const uint32_t* __restrict__ p32,
-                          const uint64_t* __restrict__ aid, uint32_t count, uint32_t step_cap,
-                          uint32_t* __restrict__ len, uint32_t* __restrict__ status) {
+__global__ void k_hit_len(const uint4* __restrict__ node, const uint4* __restrict__ erec, const uint4* __restrict__ grec,
+                          uint32_t n, uint32_t k0, uint32_t k1, const uint32_t* __restrict__ s_bits,
+                          const uint32_t* __restrict__ p32, const uint64_t* __restrict__ aid, uint32_t count,
+                          uint32_t step_cap, uint32_t* __restrict__ len, uint32_t* __restrict__ status) {
   for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < count; h += gridDim.x * blockDim.x) {
     const uint64_t a = aid[h];
     uint32_t v = start_node(a, n, k0, k1), l = 1;
+    uint4 rec = __ldg(&node[v]);
     for (;;) {
       const uint4 x = node_draw(a, v, k0, k1);
       if (((__ldg(&s_bits[v >> 5]) >> (v & 31)) & 1u) && (!HAS_P || source_coin(x.y, __ldg(&p32[v])))) break;
-      const uint4 nd = __ldg(&node[v]);
-      if (x.x >= nd.w || l >= step_cap) {
+      if (x.x >= rec.w || l >= step_cap) {
         atomicOr(status, 2u);
         break;
       }
-      v = __ldg(&edge[nd.x + pick_in_edge(edge, nd, x.x)].x);
+      uint4 ra, rb;
+      record_step(erec, grec, rec, x.x, ra, rb);
+      v = ra.x;
+      rec = make_uint4(ra.y, ra.z, ra.w, rb.x);
       ++l;
     }
     len[h] = l;
@@ -329,11 +332,11 @@ hsaw_status pool_hits(const Graph& g, const QueryDev& qd, Stream& st, uint64_t a
   const unsigned hgrid = grid_for(h, 128, 1u << 16);
   count_launch();
   if (qd.p32)
-    k_hit_len<true><<<hgrid, 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, k0, k1, qd.s_bits, qd.p32,
+    k_hit_len<true><<<hgrid, 128, 0, s>>>(g.node, g.erec, g.grec, (uint32_t)g.n, k0, k1, qd.s_bits, qd.p32,
                                           st.aid.p + st.count, h, pool_step_cap(g), st.len.p + st.count,
                                           st.ctrs.p + 3);
   else
-    k_hit_len<false><<<hgrid, 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, k0, k1, qd.s_bits, nullptr,
+    k_hit_len<false><<<hgrid, 128, 0, s>>>(g.node, g.erec, g.grec, (uint32_t)g.n, k0, k1, qd.s_bits, nullptr,
                                            st.aid.p + st.count, h, pool_step_cap(g), st.len.p + st.count,
                                            st.ctrs.p + 3);
   HSAW_CK(cudaGetLastError());

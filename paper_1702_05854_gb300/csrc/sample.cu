@@ -201,24 +201,26 @@ __global__ void k_offsets(const uint64_t* __restrict__ excl, int64_t n, int64_t 
 }
 
 // Re-derive hit walks from their attempt ids (path encoding) into the flat buffers.
-__global__ void k_rewalk(const uint4* __restrict__ node, const uint2* __restrict__ edge, uint32_t n, uint32_t k0,
-                         uint32_t k1, const uint64_t* __restrict__ aid, const uint32_t* __restrict__ len,
-                         const int64_t* __restrict__ node_off, int64_t h0, int64_t h1, int32_t* __restrict__ nodes,
-                         int32_t* __restrict__ edges) {
+__global__ void k_rewalk(const uint4* __restrict__ node, const uint4* __restrict__ erec, const uint4* __restrict__ grec,
+                         uint32_t n, uint32_t k0, uint32_t k1, const uint64_t* __restrict__ aid,
+                         const uint32_t* __restrict__ len, const int64_t* __restrict__ node_off, int64_t h0, int64_t h1,
+                         int32_t* __restrict__ nodes, int32_t* __restrict__ edges) {
   for (int64_t h = h0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < h1; h += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t a = aid[h];
     const uint32_t l = len[h];
     const int64_t nb = node_off[h], eb = nb - h;
     uint32_t v = start_node(a, n, k0, k1);
     nodes[nb] = (int32_t)v;
+    uint4 rec = l > 1 ? __ldg(&node[v]) : make_uint4(0, 0, 0, 0);
     for (uint32_t i = 1; i < l; ++i) {
       const uint4 x = node_draw(a, v, k0, k1);
-      const uint4 nd = __ldg(&node[v]);
-      const uint32_t e = nd.x + pick_in_edge(edge, nd, x.x);
-      const uint32_t u = __ldg(&edge[e].x);
-      nodes[nb + i] = (int32_t)u;
+      if (x.x >= rec.w) break;  // a hit's walk has a live in-edge at each of its first l - 1 nodes
+      uint4 ra, rb;
+      const uint32_t e = record_step(erec, grec, rec, x.x, ra, rb);
+      nodes[nb + i] = (int32_t)ra.x;
       edges[eb + i - 1] = (int32_t)e;
-      v = u;
+      v = ra.x;
+      rec = make_uint4(ra.y, ra.z, ra.w, rb.x);
     }
   }
 }
@@ -567,7 +569,8 @@ hsaw_status stream_take_hits(const Graph& g, const QueryDev& qd, Stream& st, uin
   HSAW_TRY(st.nodes.ensure((size_t)tot, s, true));
   HSAW_TRY(st.edges.ensure((size_t)tot, s, true));
   count_launch();
-  k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.edge, (uint32_t)g.n, k0, k1, st.aid.p, st.len.p,
+  k_rewalk<<<grid_for(new_hits, 128, 1u << 16), 128, 0, s>>>(g.node, g.erec, g.grec, (uint32_t)g.n, k0, k1, st.aid.p,
+                                                               st.len.p,
                                                                st.node_off.p, st.count, st.count + new_hits,
                                                                st.nodes.p, st.edges.p);
   HSAW_CK(cudaGetLastError());
