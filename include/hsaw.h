@@ -323,6 +323,25 @@ HSAW_API hsaw_status hsaw_profile_read(hsaw_profile* out);
 HSAW_API hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, uint32_t steps, int32_t blocks_per_sm,
                                        double* reads_per_s, double* ms, void* stream);
 
+/* ------------------------------------------------------------------ device scratch
+ * The paper has no counterpart to this call.  Scratch device memory (a solve's walk
+ * streams, histograms, inverted index and greedy state; not graphs, walk pools or the
+ * static sampler scratch) comes from CUDA's stream-ordered memory pool unless the caller
+ * installs an allocator of its own, such as a framework's caching allocator:
+ *   alloc(bytes, stream, ctx) returns device memory on the current device, aligned to at
+ *     least 256 bytes, usable in stream order on `stream`, or NULL when it has none (the
+ *     call in progress then fails with HSAW_E_NOMEM);
+ *   release(ptr, stream, ctx) takes back a block alloc returned, in stream order on
+ *     `stream`.
+ * The library calls them from whichever thread runs the call (batch and server workers
+ * too), one at a time.  The allocator is process-wide; alloc = release = NULL restores the
+ * pool.  Errors: HSAW_E_INVALID if exactly one of alloc and release is NULL, or while the
+ * library still holds scratch blocks of the current allocator (a live hsaw_walks handle,
+ * a server, a call in progress), since each block must go back where it came from. */
+typedef void* (*hsaw_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*hsaw_free_fn)(void* ptr, void* stream, void* ctx);
+HSAW_API hsaw_status hsaw_set_allocator(hsaw_alloc_fn alloc, hsaw_free_fn release, void* ctx);
+
 /* ------------------------------------------------------------------ diagnostics */
 HSAW_API const char* hsaw_last_error(void); /* thread-local message of the last failing call */
 HSAW_API const char* hsaw_version(void);

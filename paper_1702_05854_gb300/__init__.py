@@ -77,6 +77,7 @@ SIGNATURES = {
     "hsaw_estimate_spread": (ctypes.c_int, [_p, ctypes.POINTER(hsaw_query), _p, _i32, ctypes.POINTER(_dbl),
                                             ctypes.POINTER(_dbl), _p]),
     "hsaw_debug_fail_alloc_after": (ctypes.c_int, [_i64]),
+    "hsaw_set_allocator": (ctypes.c_int, [_p, _p, _p]),
     "hsaw_graph_build_walk_pool": (ctypes.c_int, [_p, _u64, _u64, _p]),
     "hsaw_graph_drop_walk_pool": (ctypes.c_int, [_p]),
     "hsaw_server_create": (ctypes.c_int, [_p, _i32, ctypes.c_size_t, _i32, ctypes.POINTER(_p)]),
@@ -217,6 +218,49 @@ def hsaw_estimate_spread(graph, query, removed=None, stream=None):
     _check(load().hsaw_estimate_spread(graph.handle, ctypes.byref(q), _ptr(rem) if rem.size else None, rem.size,
                                        ctypes.byref(sp), ctypes.byref(se), _stream(stream)))
     return sp.value, se.value
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None  # the installed callbacks, kept alive while the library holds them
+
+
+def hsaw_set_allocator(alloc=None, release=None):
+    """Scratch device memory from alloc(nbytes, stream) -> device pointer (an int; 0 when
+    out of memory) and release(ptr, stream), stream being the raw cudaStream_t as an int;
+    with no arguments, from CUDA's stream-ordered pool again.  Refused (HsawError) while
+    the library still holds scratch of the current allocator."""
+    global _allocator_refs
+    if alloc is None and release is None:
+        _check(load().hsaw_set_allocator(None, None, None))
+        _allocator_refs = None
+        return
+    if alloc is None or release is None:
+        raise ValueError("give both alloc and release, or neither")
+
+    def a(nbytes, stream, ctx):
+        try:
+            return alloc(int(nbytes), stream or 0) or None
+        except Exception:  # the library reports HSAW_E_NOMEM
+            return None
+
+    def r(ptr, stream, ctx):
+        release(ptr, stream or 0)
+
+    fa, fr = _ALLOC_FN(a), _FREE_FN(r)
+    _check(load().hsaw_set_allocator(ctypes.cast(fa, ctypes.c_void_p), ctypes.cast(fr, ctypes.c_void_p), None))
+    _allocator_refs = (fa, fr)
+
+
+def use_torch_allocator(on: bool = True):
+    """Take the library's scratch from torch's caching allocator (on the stream the library
+    runs on), or (on=False) from CUDA's pool again."""
+    if not on:
+        hsaw_set_allocator()
+        return
+    import torch
+    hsaw_set_allocator(lambda nbytes, stream: torch.cuda.caching_allocator_alloc(nbytes, stream=stream),
+                       lambda ptr, stream: torch.cuda.caching_allocator_delete(ptr))
 
 
 def hsaw_debug_fail_alloc_after(n: int):

@@ -29,11 +29,38 @@ hsaw_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
 
 static std::once_flag g_pool_once;
 static std::atomic<long long> g_fail_countdown{0};  // test hook: > 0 counts down to a failing allocation
+
+// Scratch allocator: CUDA's stream-ordered pool, or the caller's (hsaw_set_allocator).
+// Allocation, release and a change of allocator hold one lock, and the allocator changes
+// only while no scratch block is held, so every block goes back to the allocator it came
+// from.
+struct ScratchAllocator {
+  hsaw_alloc_fn alloc = nullptr;
+  hsaw_free_fn release = nullptr;
+  void* ctx = nullptr;
+};
+static std::mutex g_alloc_mu;
+static ScratchAllocator g_alloc;
+static long long g_held = 0;  // scratch blocks handed out and not yet released
+
 hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
   if (g_fail_countdown.load(std::memory_order_relaxed) > 0 && g_fail_countdown.fetch_sub(1) == 1) {
     *p = nullptr;
     t_err = "device allocation failed (injected by hsaw_debug_fail_alloc_after)";
     return HSAW_E_NOMEM;
+  }
+  if (bytes == 0) bytes = 16;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (g_alloc.alloc) {
+    *p = g_alloc.alloc(bytes, (void*)s, g_alloc.ctx);
+    if (!*p) {
+      char buf[128];
+      snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed (caller's allocator)", bytes);
+      t_err = buf;
+      return HSAW_E_NOMEM;
+    }
+    ++g_held;
+    return HSAW_OK;
   }
   std::call_once(g_pool_once, [] {
     int dev = 0;
@@ -44,7 +71,6 @@ hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
   });
-  if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -54,10 +80,17 @@ hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
     t_err = buf;
     return HSAW_E_NOMEM;
   }
+  ++g_held;
   return HSAW_OK;
 }
 void dfree(void* p, cudaStream_t s) {
-  if (p) cudaFreeAsync(p, s);
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (g_alloc.release)
+    g_alloc.release(p, (void*)s, g_alloc.ctx);
+  else
+    cudaFreeAsync(p, s);
+  --g_held;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -490,6 +523,22 @@ hsaw_status hsaw_graph_destroy(hsaw_graph g) {
   sample_tune_forget(g->g);
   destroy_graph(g->g);
   delete g;
+  return HSAW_OK;
+}
+
+hsaw_status hsaw_set_allocator(hsaw_alloc_fn alloc, hsaw_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(HSAW_E_INVALID, "allocator: give both alloc and release, or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (g_held != 0) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "allocator: %lld scratch blocks of the current allocator are still held", g_held);
+    t_err = buf;
+    return HSAW_E_INVALID;
+  }
+  g_alloc.alloc = alloc;
+  g_alloc.release = release;
+  g_alloc.ctx = alloc ? ctx : nullptr;
   return HSAW_OK;
 }
 

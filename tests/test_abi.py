@@ -41,7 +41,7 @@ def test_built_for_sm103a():
 _SCALAR = {"int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64, "int32_t": ctypes.c_int32,
            "uint32_t": ctypes.c_uint32, "int": ctypes.c_int, "double": ctypes.c_double, "size_t": ctypes.c_size_t,
            "hsaw_mode": ctypes.c_int, "hsaw_sampling": ctypes.c_int}
-_OPAQUE = {"hsaw_graph", "hsaw_walks", "hsaw_server"}
+_OPAQUE = {"hsaw_graph", "hsaw_walks", "hsaw_server", "hsaw_alloc_fn", "hsaw_free_fn"}
 
 
 def _strip_comments(text):
@@ -102,3 +102,16 @@ def test_structs_match_declarations():
     for cname, pyc in (("hsaw_query", hs.hsaw_query), ("hsaw_result", hs.hsaw_result),
                        ("hsaw_profile", hs.hsaw_profile)):
         assert _struct_fields(cname) == [f for f, _ in pyc._fields_], cname
+
+
+def test_set_allocator_checks_its_arguments():
+    """Installing a scratch allocator needs both callbacks (or neither); the registration
+    itself makes no device call."""
+    lib = hs.load()
+    fa = hs._ALLOC_FN(lambda nbytes, stream, ctx: None)
+    fr = hs._FREE_FN(lambda ptr, stream, ctx: None)
+    as_ptr = lambda f: ctypes.cast(f, ctypes.c_void_p)  # noqa: E731
+    assert lib.hsaw_set_allocator(as_ptr(fa), None, None) == -1
+    assert lib.hsaw_set_allocator(None, as_ptr(fr), None) == -1
+    assert lib.hsaw_set_allocator(as_ptr(fa), as_ptr(fr), None) == 0
+    assert lib.hsaw_set_allocator(None, None, None) == 0
