@@ -333,11 +333,13 @@ HSAW_API hsaw_status hsaw_probe_gather(uint64_t table_bytes, int32_t chains, uin
  *     call in progress then fails with HSAW_E_NOMEM);
  *   release(ptr, stream, ctx) takes back a block alloc returned, in stream order on
  *     `stream`.
- * The library calls them from whichever thread runs the call (batch and server workers
- * too), one at a time.  The allocator is process-wide; alloc = release = NULL restores the
- * pool.  Errors: HSAW_E_INVALID if exactly one of alloc and release is NULL, or while the
- * library still holds scratch blocks of the current allocator (a live hsaw_walks handle,
- * a server, a call in progress), since each block must go back where it came from. */
+ * The library calls them from whichever threads run its calls (batch and server workers
+ * too), possibly at the same time, so they must be thread-safe.  The allocator is
+ * process-wide; alloc = release = NULL restores the pool.  Call this while no other
+ * library call is in progress.  Errors: HSAW_E_INVALID if exactly one of alloc and
+ * release is NULL, or while the library still holds scratch blocks of the current
+ * allocator (a live hsaw_walks handle, a server), since each block must go back where it
+ * came from. */
 typedef void* (*hsaw_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*hsaw_free_fn)(void* ptr, void* stream, void* ctx);
 HSAW_API hsaw_status hsaw_set_allocator(hsaw_alloc_fn alloc, hsaw_free_fn release, void* ctx);

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -30,18 +31,18 @@ hsaw_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
 static std::once_flag g_pool_once;
 static std::atomic<long long> g_fail_countdown{0};  // test hook: > 0 counts down to a failing allocation
 
-// Scratch allocator: CUDA's stream-ordered pool, or the caller's (hsaw_set_allocator).
-// Allocation, release and a change of allocator hold one lock, and the allocator changes
-// only while no scratch block is held, so every block goes back to the allocator it came
-// from.
+// Scratch allocator: CUDA's stream-ordered pool, or the caller's (hsaw_set_allocator).  The
+// allocator changes only while no scratch block is held and no other call runs, so every
+// block goes back to the allocator it came from; allocations read it without a lock.
 struct ScratchAllocator {
-  hsaw_alloc_fn alloc = nullptr;
-  hsaw_free_fn release = nullptr;
-  void* ctx = nullptr;
+  hsaw_alloc_fn alloc;
+  hsaw_free_fn release;
+  void* ctx;
 };
-static std::mutex g_alloc_mu;
-static ScratchAllocator g_alloc;
-static long long g_held = 0;  // scratch blocks handed out and not yet released
+static std::mutex g_alloc_set_mu;                          // serialises changes
+static std::vector<std::unique_ptr<ScratchAllocator>> g_alloc_all;  // every one installed, kept to exit
+static std::atomic<const ScratchAllocator*> g_alloc{nullptr};
+static std::atomic<long long> g_held{0};                   // scratch blocks handed out, not yet released
 
 hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
   if (g_fail_countdown.load(std::memory_order_relaxed) > 0 && g_fail_countdown.fetch_sub(1) == 1) {
@@ -50,16 +51,15 @@ hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
     return HSAW_E_NOMEM;
   }
   if (bytes == 0) bytes = 16;
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
-  if (g_alloc.alloc) {
-    *p = g_alloc.alloc(bytes, (void*)s, g_alloc.ctx);
+  if (const ScratchAllocator* a = g_alloc.load(std::memory_order_acquire)) {
+    *p = a->alloc(bytes, (void*)s, a->ctx);
     if (!*p) {
       char buf[128];
       snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed (caller's allocator)", bytes);
       t_err = buf;
       return HSAW_E_NOMEM;
     }
-    ++g_held;
+    g_held.fetch_add(1);
     return HSAW_OK;
   }
   std::call_once(g_pool_once, [] {
@@ -80,17 +80,16 @@ hsaw_status dmalloc(void** p, size_t bytes, cudaStream_t s) {
     t_err = buf;
     return HSAW_E_NOMEM;
   }
-  ++g_held;
+  g_held.fetch_add(1);
   return HSAW_OK;
 }
 void dfree(void* p, cudaStream_t s) {
   if (!p) return;
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
-  if (g_alloc.release)
-    g_alloc.release(p, (void*)s, g_alloc.ctx);
+  if (const ScratchAllocator* a = g_alloc.load(std::memory_order_acquire))
+    a->release(p, (void*)s, a->ctx);
   else
     cudaFreeAsync(p, s);
-  --g_held;
+  g_held.fetch_sub(1);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -529,16 +528,20 @@ hsaw_status hsaw_graph_destroy(hsaw_graph g) {
 hsaw_status hsaw_set_allocator(hsaw_alloc_fn alloc, hsaw_free_fn release, void* ctx) {
   if ((alloc == nullptr) != (release == nullptr))
     return fail(HSAW_E_INVALID, "allocator: give both alloc and release, or neither");
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
-  if (g_held != 0) {
+  std::lock_guard<std::mutex> lk(g_alloc_set_mu);
+  const long long held = g_held.load();
+  if (held != 0) {
     char buf[160];
-    snprintf(buf, sizeof(buf), "allocator: %lld scratch blocks of the current allocator are still held", g_held);
+    snprintf(buf, sizeof(buf), "allocator: %lld scratch blocks of the current allocator are still held", held);
     t_err = buf;
     return HSAW_E_INVALID;
   }
-  g_alloc.alloc = alloc;
-  g_alloc.release = release;
-  g_alloc.ctx = alloc ? ctx : nullptr;
+  const ScratchAllocator* next = nullptr;
+  if (alloc) {
+    g_alloc_all.emplace_back(new ScratchAllocator{alloc, release, ctx});
+    next = g_alloc_all.back().get();
+  }
+  g_alloc.store(next, std::memory_order_release);
   return HSAW_OK;
 }
 
