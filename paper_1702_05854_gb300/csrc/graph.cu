@@ -95,12 +95,9 @@ void dfree(void* p, cudaStream_t s) {
 // ------------------------------------------------------------------ kernels
 enum : uint32_t { ERR_RANGE = 1u, ERR_WEIGHT = 2u, ERR_ROWPTR = 4u };
 
-__global__ void k_validate_edges(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                 int64_t n, uint32_t* __restrict__ err) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t a = src[e], b = dst[e];
-    if (a < 0 || a >= n || b < 0 || b >= n) atomicOr(err, ERR_RANGE);
-  }
+__global__ void k_validate_nodes(const int32_t* __restrict__ a, int64_t m, int64_t n, uint32_t* __restrict__ err) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    if (a[e] < 0 || a[e] >= n) atomicOr(err, ERR_RANGE);
 }
 
 __global__ void k_iota_dst(const int32_t* __restrict__ dst, int64_t m, uint32_t* __restrict__ keys,
@@ -301,6 +298,25 @@ static hsaw_status alloc_graph(Graph& g, int64_t n, int64_t m, bool with_index) 
   return HSAW_OK;
 }
 
+// A second stream (with one event) for copies that overlap work on the call's stream; it is
+// drained and destroyed when the call returns, before its temporaries are freed.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  hsaw_status create() {
+    HSAW_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    HSAW_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    return HSAW_OK;
+  }
+  ~SideStream() {
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+    if (ev) cudaEventDestroy(ev);
+  }
+};
+
 struct Temps {
   std::vector<void*> ptrs;
   cudaStream_t s;
@@ -363,21 +379,20 @@ static hsaw_status from_edges(int64_t n, int64_t m, const int32_t* src, const in
   if (m > 0 && (!src || !dst || !w)) return fail(HSAW_E_INVALID, "graph: NULL edge array");
   const bool dev = flags & HSAW_INPUT_DEVICE;
   Temps T(s);
+  // host input: the destinations are copied first and sorted on s while the sources and
+  // weights are copied on a side stream (the side stream is drained before T frees)
+  SideStream side;
   int32_t *d_src = nullptr, *d_dst = nullptr;
   uint32_t* d_w = nullptr;
   bool o1, o2, o3;
-  HSAW_TRY(stage(src, (size_t)m, dev, s, &d_src, &o1));
-  if (o1) T.keep(d_src);
   HSAW_TRY(stage(dst, (size_t)m, dev, s, &d_dst, &o2));
   if (o2) T.keep(d_dst);
-  HSAW_TRY(stage(w, (size_t)m, dev, s, &d_w, &o3));
-  if (o3) T.keep(d_w);
   uint32_t* d_err = nullptr;
   HSAW_TRY(T.get(&d_err, 1));
   HSAW_CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
   if (m) {
     count_launch();
-    k_validate_edges<<<grid_for(m, 256, 8192), 256, 0, s>>>(d_src, d_dst, m, n, d_err);
+    k_validate_nodes<<<grid_for(m, 256, 8192), 256, 0, s>>>(d_dst, m, n, d_err);
     HSAW_CK(cudaGetLastError());
     HSAW_TRY(check_err(d_err, s));
   }
@@ -399,6 +414,25 @@ static hsaw_status from_edges(int64_t n, int64_t m, const int32_t* src, const in
   count_launch();
   k_row_from_sorted<<<grid_for(n + 1, 256, 8192), 256, 0, s>>>(sk, m, n, row_start);
   HSAW_CK(cudaGetLastError());
+  cudaStream_t cs = s;
+  if (!dev && m) {  // the destinations' copy finished at the validation's synchronisation
+    HSAW_TRY(side.create());
+    cs = side.s;
+  }
+  HSAW_TRY(stage(src, (size_t)m, dev, cs, &d_src, &o1));
+  if (o1) T.keep(d_src);
+  HSAW_TRY(stage(w, (size_t)m, dev, cs, &d_w, &o3));
+  if (o3) T.keep(d_w);
+  if (cs != s) {
+    HSAW_CK(cudaEventRecord(side.ev, cs));
+    HSAW_CK(cudaStreamWaitEvent(s, side.ev, 0));
+  }
+  if (m) {
+    count_launch();
+    k_validate_nodes<<<grid_for(m, 256, 8192), 256, 0, s>>>(d_src, m, n, d_err);
+    HSAW_CK(cudaGetLastError());
+    HSAW_TRY(check_err(d_err, s));
+  }
   HSAW_TRY(alloc_graph(g, n, m, true));
   if (m) {
     count_launch();
