@@ -252,6 +252,16 @@ static hsaw_status check_err(uint32_t* d_err, cudaStream_t s) {
   return HSAW_OK;
 }
 
+// True for page-locked (pinned or registered) host memory, whose copies run asynchronously.
+static bool host_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 template <typename T>
 static hsaw_status stage(const T* p, size_t count, bool on_device, cudaStream_t s, T** dev, bool* owned) {
   *owned = false;
@@ -379,12 +389,20 @@ static hsaw_status from_edges(int64_t n, int64_t m, const int32_t* src, const in
   if (m > 0 && (!src || !dst || !w)) return fail(HSAW_E_INVALID, "graph: NULL edge array");
   const bool dev = flags & HSAW_INPUT_DEVICE;
   Temps T(s);
-  // host input: the destinations are copied first and sorted on s while the sources and
-  // weights are copied on a side stream (the side stream is drained before T frees)
+  // pinned host input: the destinations are copied first and sorted on s while the
+  // sources and weights are copied on a side stream (drained before T frees); pageable
+  // input is copied first, all of it, on s (its copies do not overlap kernels)
   SideStream side;
+  const bool overlap = !dev && m > 0 && host_pinned(src) && host_pinned(w);
   int32_t *d_src = nullptr, *d_dst = nullptr;
   uint32_t* d_w = nullptr;
-  bool o1, o2, o3;
+  bool o1 = false, o2 = false, o3 = false;
+  if (!overlap) {
+    HSAW_TRY(stage(src, (size_t)m, dev, s, &d_src, &o1));
+    if (o1) T.keep(d_src);
+    HSAW_TRY(stage(w, (size_t)m, dev, s, &d_w, &o3));
+    if (o3) T.keep(d_w);
+  }
   HSAW_TRY(stage(dst, (size_t)m, dev, s, &d_dst, &o2));
   if (o2) T.keep(d_dst);
   uint32_t* d_err = nullptr;
@@ -393,6 +411,10 @@ static hsaw_status from_edges(int64_t n, int64_t m, const int32_t* src, const in
   if (m) {
     count_launch();
     k_validate_nodes<<<grid_for(m, 256, 8192), 256, 0, s>>>(d_dst, m, n, d_err);
+    if (!overlap) {
+      count_launch();
+      k_validate_nodes<<<grid_for(m, 256, 8192), 256, 0, s>>>(d_src, m, n, d_err);
+    }
     HSAW_CK(cudaGetLastError());
     HSAW_TRY(check_err(d_err, s));
   }
@@ -414,20 +436,14 @@ static hsaw_status from_edges(int64_t n, int64_t m, const int32_t* src, const in
   count_launch();
   k_row_from_sorted<<<grid_for(n + 1, 256, 8192), 256, 0, s>>>(sk, m, n, row_start);
   HSAW_CK(cudaGetLastError());
-  cudaStream_t cs = s;
-  if (!dev && m) {  // the destinations' copy finished at the validation's synchronisation
+  if (overlap) {  // the destinations' copy finished at the validation's synchronisation
     HSAW_TRY(side.create());
-    cs = side.s;
-  }
-  HSAW_TRY(stage(src, (size_t)m, dev, cs, &d_src, &o1));
-  if (o1) T.keep(d_src);
-  HSAW_TRY(stage(w, (size_t)m, dev, cs, &d_w, &o3));
-  if (o3) T.keep(d_w);
-  if (cs != s) {
-    HSAW_CK(cudaEventRecord(side.ev, cs));
+    HSAW_TRY(stage(src, (size_t)m, dev, side.s, &d_src, &o1));
+    if (o1) T.keep(d_src);
+    HSAW_TRY(stage(w, (size_t)m, dev, side.s, &d_w, &o3));
+    if (o3) T.keep(d_w);
+    HSAW_CK(cudaEventRecord(side.ev, side.s));
     HSAW_CK(cudaStreamWaitEvent(s, side.ev, 0));
-  }
-  if (m) {
     count_launch();
     k_validate_nodes<<<grid_for(m, 256, 8192), 256, 0, s>>>(d_src, m, n, d_err);
     HSAW_CK(cudaGetLastError());

@@ -90,6 +90,22 @@ def test_graph_ingest_errors():
     assert e.value.status == -1
 
 
+def test_graph_ingest_from_pinned_host_memory(rmat14):
+    """Pinned host arrays take the other copy order (destinations first and sorted while
+    sources and weights are copied on a side stream): the same graph, and the same range
+    errors for bad sources or destinations."""
+    d, _, og = rmat14
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+    src, dst, w = pin(d["src"]), pin(d["dst"]), pin(d["w"])
+    assert_graph_equal(hs.hsaw_graph_from_edges(d["n"], src, dst, w), og)
+    for bad_src in (True, False):
+        s2, d2 = pin(d["src"].copy()), pin(d["dst"].copy())
+        (s2 if bad_src else d2)[len(s2) // 2] = d["n"]
+        with pytest.raises(hs.HsawError) as e:
+            hs.hsaw_graph_from_edges(d["n"], s2, d2, w)
+        assert e.value.status == -3
+
+
 def test_graph_from_csr_matches(c1):
     d, g, og = c1
     rp, s, dd, thr, ii = og.arrays()
